@@ -1,0 +1,357 @@
+"""Benchmark of the D4orm denoising hot path on GB300.
+
+One bench step = one full anytime solve (Algorithm 2: `iters` iterations of
+`K` denoising steps, each step = sample rollout + fitness of N samples,
+softmax weights, weighted-mean update; then apply + rollout + verdict) of the
+selected synthetic workload.  Metric: sample-rollouts/s (rollout+fitness),
+i.e. N * K * iters sample rollouts per step / step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+
+Default workload: 8 unicycle robots on a 4 m circle with antipodal goals and
++-0.3 m jitter, T = 100, N = 2048, 100 steps x 5 iterations.
+Multi-GPU (torchrun): every rank solves its own replica (independent
+instances, weak scaling); value = all ranks' sample rollouts / max time.
+
+`--impl reference` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (the comparison arm; the paper ships no code).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import scenarios  # noqa: E402
+
+METRIC = "sample-rollouts/s (rollout+fitness)"
+UNIT = "sample-rollouts/s"
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="unicycle_n8", choices=sorted(scenarios.WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def f32_inst(inst):
+    inst.start = inst.start.astype(np.float32).astype(np.float64)
+    inst.goal = inst.goal.astype(np.float32).astype(np.float64)
+    return inst
+
+
+# ---------------------------------------------------------------------------
+# algorithmic FP32 work of one sample rollout + fitness (FFMA = 2 flops,
+# FADD/FMUL/FMNMX/FSETP/MUFU = 1), counted from the method, not the kernel:
+#   per robot-timestep: sample u = clip(M + sigma eps): 4 d_u;
+#                       Box-Muller per normal: 5;
+#                       dynamics step: holonomic 8 d_p, unicycle 31, diff-drive 37;
+#                       goal term of Eq. (4) + accumulation: 3 d_p + 4;
+#   per unordered robot pair and timestep (Eq. (5)): 3 d_p + 1.
+# ---------------------------------------------------------------------------
+DYN_FLOPS = {scenarios.HOLO2D: 16, scenarios.HOLO3D: 24, scenarios.UNICYCLE: 31, scenarios.DIFFDRIVE4: 37}
+
+
+def flops_per_sample_rollout(inst) -> int:
+    d_x, d_u, d_p = inst.dims
+    per_robot = 4 * d_u + 5 * d_u + DYN_FLOPS[inst.dyn] + 3 * d_p + 4
+    per_pair = 3 * d_p + 1
+    return inst.T * (inst.n * per_robot + inst.n * (inst.n - 1) // 2 * per_pair)
+
+
+def fp32_peak_tflops(sm_count: int, clock_mhz: float) -> float:
+    # 128 FP32 lanes per SM, FFMA = 2 flops
+    return sm_count * 128 * 2 * clock_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(torch):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(torch, world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(torch, world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_rate(inst, budget_s: float = 15.0, n_sample: int | None = None) -> dict:
+    """The oracle, as it stands, on a bounded sample: one denoising step over
+    the first n_sample samples (fitness of each, weights, weighted-mean
+    update), repeated until ~budget_s of CPU time; single thread."""
+    import oracle
+    op = oracle.Problem(n=inst.n, T=inst.T, dyn=inst.dyn, integ=inst.integ, dt=inst.dt, radius=inst.radius,
+                        start=inst.start, goal=inst.goal, u_lo=inst.u_lo, u_hi=inst.u_hi,
+                        eps_margin=inst.eps_margin, goal_tol=inst.goal_tol, v_max=inst.v_max)
+    d_u = inst.dims[1]
+    rng = np.random.default_rng(0)
+    u_base = scenarios.random_controls(rng, inst, 0.5)
+    du = scenarios.random_deformation(rng, inst, 0.3)
+    if n_sample is None:
+        # size the sample from a probe of 4 samples
+        pp = oracle.Params(N=4, K=inst.K, lam=inst.lam, w_safe=inst.w_safe, beta0=inst.beta0, beta1=inst.beta1,
+                           seed=inst.seed, tag=inst.tag)
+        t0 = time.perf_counter()
+        oracle.denoise_step(op, pp, 0, inst.K, u_base, du)
+        per = (time.perf_counter() - t0) / 4
+        n_sample = int(max(8, min(inst.N, budget_s / 3 / max(per, 1e-9))))
+    pp = oracle.Params(N=n_sample, K=inst.K, lam=inst.lam, w_safe=inst.w_safe, beta0=inst.beta0, beta1=inst.beta1,
+                       seed=inst.seed, tag=inst.tag)
+    done, t_total, reps = 0, 0.0, 0
+    while reps == 0 or (t_total < budget_s and reps < 1000):
+        i = inst.K - (reps % inst.K)
+        t0 = time.perf_counter()
+        oracle.denoise_step(op, pp, 0, i, u_base, du)
+        t_total += time.perf_counter() - t0
+        done += n_sample
+        reps += 1
+    return {"value": done / t_total, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} denoising step(s) of {n_sample} of the {inst.N} samples of {inst.name} "
+                      f"(fitness + weights + update, FP64, 1 thread), {t_total:.1f} s"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and rank != 0:
+        return
+    inst = f32_inst(scenarios.WORKLOADS[args.workload]())
+    per_step_budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    probe = cpu_oracle_rate(inst, budget_s=0.0, n_sample=4)
+    n_sample = int(max(8, min(inst.N, per_step_budget * probe["value"])))
+    rates = []
+    for s in range(args.warmup + args.steps):
+        r = cpu_oracle_rate(inst, budget_s=1e-9, n_sample=n_sample)  # exactly one step of n_sample samples
+        if s >= args.warmup:
+            rates.append(r["value"])
+    value = float(np.mean(rates))
+    ms = n_sample / value * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": inst.name, "samples_per_step": n_sample, "of_N": inst.N,
+                       "threads": 1},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"one denoising step over {n_sample} of {inst.N} samples per bench step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_setup(torch)
+    if rank == 0:
+        import importlib.util
+        spec = importlib.util.spec_from_file_location(
+            "d4orm_build", os.path.join(ROOT, "paper_2503_12204_gb300", "_build.py"))
+        mod = importlib.util.module_from_spec(spec)
+        spec.loader.exec_module(mod)
+        mod.build()
+    barrier(torch, world)
+    import paper_2503_12204_gb300 as g
+
+    inst = f32_inst(scenarios.WORKLOADS[args.workload]())
+    inst.tag = rank  # each rank solves its own replica
+    d_x, d_u, d_p = inst.dims
+    prob = g.Problem(inst)
+    params = g.Params(n_samples=inst.N, n_steps=inst.K, temperature=inst.lam, w_safe=inst.w_safe,
+                      beta0=inst.beta0, beta1=inst.beta1, seed=inst.seed, instance_tag=inst.tag)
+    budget = g.Budget(max_iters=inst.iters)
+    stream = torch.cuda.current_stream()
+    u_out = torch.zeros((inst.T, inst.n, d_u), device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    rollouts_per_step = inst.N * inst.K * inst.iters
+    launches_per_step = inst.iters * (4 * inst.K + 1)
+
+    for _ in range(args.warmup):
+        g.d4orm_solve(prob.handle, params, budget, u_out, stream=stream)
+    torch.cuda.synchronize()
+
+    # ---------------- timed region: K solves on device-resident inputs
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    results = []
+    barrier(torch, world)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        for s in range(args.steps):
+            flush.zero_()  # L2 flush between timed steps (outside the events)
+            ev[s][0].record(stream)
+            results.append(g.d4orm_solve(prob.handle, params, budget, u_out, stream=stream))
+            ev[s][1].record(stream)
+        torch.cuda.synchronize()
+    barrier(torch, world)
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    ms = max_over_ranks(torch, world, ms)
+    value = rollouts_per_step * world / (ms / 1e3)
+
+    # ---------------- end to end through the C ABI with host buffers
+    start_h = torch.tensor(inst.start, dtype=torch.float32).pin_memory()
+    goal_h = torch.tensor(inst.goal, dtype=torch.float32).pin_memory()
+    u_h = torch.empty((inst.T, inst.n, d_u), dtype=torch.float32).pin_memory()
+    e2e_ms = []
+    for s in range(max(2, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = g.d4orm_problem_create(inst.n, inst.T, inst.dyn, inst.integ, inst.dt, inst.radius, start_h.numpy(),
+                                   goal_h.numpy(), eps_margin=inst.eps_margin, goal_tol=inst.goal_tol,
+                                   v_max=inst.v_max, u_lo=inst.u_lo, u_hi=inst.u_hi)
+        r = g.d4orm_solve(h, params, budget, u_out, stream=stream)
+        u_h.copy_(u_out, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        g.d4orm_problem_destroy(h)
+    e2e = max_over_ranks(torch, world, statistics.median(e2e_ms))
+    h2d = 2 * inst.n * d_x * 4
+    d2h = inst.T * inst.n * d_u * 4 + 40  # plan + result struct
+
+    # ---------------- per-kernel breakdown (same kernels, same launch shapes)
+    nctrl = (inst.T, inst.n, d_u)
+    du_a = torch.zeros(nctrl, device="cuda")
+    du_b = torch.zeros(nctrl, device="cuda")
+    base = torch.zeros(nctrl, device="cuda")
+    kms = []
+    for i in range(inst.K, 0, -1):
+        kms.append(g.d4orm_denoise_step_timed(prob.handle, params, 0, i, base, du_a, du_b, stream=stream))
+        du_a, du_b = du_b, du_a
+    kms = np.array(kms)
+    k2_ms = float(kms[:, 0].mean())
+    step_ms = float(kms.sum(axis=1).mean())
+    share = (kms.mean(axis=0) / kms.mean(axis=0).sum()).tolist()
+    flops = flops_per_sample_rollout(inst) * inst.N
+    props = torch.cuda.get_device_properties(0)
+    csum = clocks.summary()
+    peak = fp32_peak_tflops(props.multi_processor_count, 2070.0)
+    achieved = flops / (k2_ms / 1e3) / 1e12
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": inst.name, "dynamics": scenarios.DYN_NAMES[inst.dyn], "robots": inst.n,
+                   "horizon_T": inst.T, "samples_N": inst.N, "denoise_steps": inst.K, "iterations": inst.iters,
+                   "sample_rollouts_per_step": rollouts_per_step, "parallelism": f"replicas{world}",
+                   "l2": "flushed between timed steps (256 MB write)"},
+        "e2e": {"value": rollouts_per_step * world / (e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": csum,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_rollout_fitness", "peak_basis": "FP32 lanes x 2 x 2070 MHz (152 SMs x 128)",
+                     "flops_per_launch": flops, "launch_ms": k2_ms},
+        "kernel_share": {"rollout_fitness": share[0], "softmax_weights": share[1], "weighted_sum": share[2],
+                         "finalize": share[3], "eager_step_ms": step_ms},
+        "verdict": results[-1]["verdict"],
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_rate(inst, budget_s=15.0)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    prob.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,210 @@
+/*
+ * d4orm.h -- C ABI of the GB300 (sm_103a) D4orm denoising library.
+ *
+ * D4orm (Zhang et al., IROS 2025) plans collision-free multi-robot
+ * trajectories by diffusion-style denoising of a control deformation:
+ * each denoising step draws N Monte Carlo deformation samples around the
+ * current one (Eq. (12)), rolls every sample's robot team out through the
+ * dynamics (Sec. III Eq. (1), Sec. V), scores it with the team reward
+ * (Eq. (3)-(5)), and replaces the deformation by a softmax-weighted mean of
+ * the samples (Eq. (6), Eq. (13), Algorithm 1).  Algorithm 2 repeats the
+ * schedule as an anytime loop around a fixed base trajectory.
+ *
+ * Conventions (all entry points):
+ *  - Plain C types only.  "_dev" pointers are CUDA device pointers owned by
+ *    the caller; "_host" pointers are host memory owned by the caller.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is stream-ordered and asynchronous unless stated.
+ *  - Argument errors are detected on the host before any launch and return
+ *    D4ORM_ERR_INVALID_ARG / D4ORM_ERR_UNSUPPORTED; nothing is launched.
+ *    CUDA failures return D4ORM_ERR_CUDA; d4orm_last_error() gives the
+ *    message of the calling thread's last failure.  Nothing throws across
+ *    the ABI and there is no CPU fallback: without a usable GPU every
+ *    compute call returns D4ORM_ERR_CUDA.
+ *  - Layouts: controls and deformations are float[T][n][d_u] (time-major,
+ *    robots contiguous); states are float[T+1][n][d_x] with states[0] = S.
+ *  - A problem handle carries device workspace (allocated on first use,
+ *    grown when N grows); calls that use one handle must not overlap in
+ *    time (issue them on one stream, or synchronise between streams).
+ *
+ * Dimensions per dynamics model (Sec. V, plus the unicycle):
+ *   HOLO2D     x=[px,py,vx,vy]          u=[ax,ay]        d_x=4 d_u=2
+ *   HOLO3D     x=[px,py,pz,vx,vy,vz]    u=[ax,ay,az]     d_x=6 d_u=3
+ *   UNICYCLE   x=[px,py,theta]          u=[v,omega]      d_x=3 d_u=2
+ *   DIFFDRIVE4 x=[px,py,theta,v]        u=[omega,a]      d_x=4 d_u=2
+ */
+#ifndef D4ORM_H
+#define D4ORM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    D4ORM_OK = 0,
+    D4ORM_ERR_INVALID_ARG = 1,  /* null pointer, size out of range, bad enum  */
+    D4ORM_ERR_UNSUPPORTED = 2,  /* valid but beyond this build's limits       */
+    D4ORM_ERR_OOM = 3,          /* device or pinned allocation failed         */
+    D4ORM_ERR_CUDA = 4,         /* a CUDA call failed (see d4orm_last_error)  */
+    D4ORM_ERR_TIMEOUT = 5,      /* a bounded device wait expired              */
+    D4ORM_ERR_CANCELLED = 6     /* cancelled by the caller                    */
+} d4orm_status;
+
+typedef enum {
+    D4ORM_DYN_HOLO2D = 0,
+    D4ORM_DYN_HOLO3D = 1,
+    D4ORM_DYN_UNICYCLE = 2,
+    D4ORM_DYN_DIFFDRIVE4 = 3
+} d4orm_dynamics;
+
+typedef enum {
+    D4ORM_INT_EULER = 0,        /* x += dt f(x, u)                           */
+    D4ORM_INT_RK4 = 1           /* classical RK4, control held over the step */
+} d4orm_integrator;
+
+#define D4ORM_MAX_ROBOTS 32         /* robots share one warp                   */
+#define D4ORM_MAX_ITERS 4096        /* iteration index fits 12 counter bits    */
+#define D4ORM_MAX_TAG ((1u << 20) - 1)
+#define D4ORM_MAX_CTRL 49152        /* T * n * d_u (mean controls in shared memory) */
+
+typedef struct d4orm_problem d4orm_problem;
+
+/* Problem of Sec. III: n robots of radius R_a, dynamics f_dyn, horizon T
+ * (the paper's H; T controls per robot, states x_0..x_T), start S and
+ * terminal state (goal; positions are what the terminal test uses). */
+typedef struct {
+    int n_robots;               /* 1..32                                      */
+    int T;                      /* >= 1                                       */
+    int dyn;                    /* d4orm_dynamics                             */
+    int integ;                  /* d4orm_integrator                           */
+    float dt;                   /* > 0                                        */
+    float radius;               /* R_a > 0                                    */
+    float eps_margin;           /* epsilon of Eq. (5), >= 0                   */
+    float goal_tol;             /* terminal-condition tolerance [m], >= 0     */
+    float v_max;                /* per-axis speed bound (holonomic; the speed
+                                   state of DIFFDRIVE4); <= 0 means none      */
+    const float *start;         /* host [n][d_x], copied at create            */
+    const float *goal;          /* host [n][d_x], copied at create            */
+    const float *u_lo;          /* host [d_u] control box, copied; NULL = the
+                                   model's default box                        */
+    const float *u_hi;          /* host [d_u]                                 */
+} d4orm_problem_desc;
+
+/* Denoising parameters (Algorithm 1, Sec. IV-B/C). */
+typedef struct {
+    int n_samples;              /* N (the paper's M), >= 1                    */
+    int n_steps;                /* K (the paper's N), 1..(1<<24)-1            */
+    float temperature;          /* lambda of Eq. (6), > 0                     */
+    float w_safe;               /* w of Eq. (3)                               */
+    float beta0, beta1;         /* linear noise schedule, 0 < beta < 1        */
+    uint64_t seed;              /* Philox key                                 */
+    uint32_t instance_tag;      /* <= D4ORM_MAX_TAG; separates instances      */
+} d4orm_params;
+
+/* Anytime budget of Algorithm 2. */
+typedef struct {
+    int max_iters;              /* 1..D4ORM_MAX_ITERS                         */
+    double deadline_ms;         /* <= 0: none; else stop after the iteration
+                                   during which it passed (host clock)       */
+    int stop_on_success;        /* stop after the first collision-free,
+                                   goal-reaching iteration                   */
+    int start_step;             /* with du_init: first iteration runs steps
+                                   start_step..1 from dU = du_init           */
+} d4orm_budget;
+
+/* Eq. (1)/(2) evaluation of one plan. */
+typedef struct {
+    int collision_free;         /* |p_k - p_l| > 2 R_a for all t in 0..T      */
+    int goal_reached;           /* |p_k[T] - goal_k| <= goal_tol for all k    */
+    float reward;               /* Eq. (3)                                    */
+    float objective;            /* Eq. (2): fraction of (k, t>=1) at goal     */
+    float min_pair_dist;        /* over t in 0..T (1e30 for one robot)        */
+} d4orm_verdict;
+
+typedef struct {
+    d4orm_verdict verdict;      /* of the returned plan                       */
+    int iters_run;
+    int first_success_iter;     /* -1 if none                                 */
+    double ms_to_success;       /* host wall clock from call entry; -1 if none*/
+    double ms_total;            /* host wall clock of the whole call          */
+} d4orm_result;
+
+/* Create a problem (Sec. III).  Copies every host array; allocates no
+ * device memory (device workspace is allocated on first compute call).
+ * Errors: INVALID_ARG for null desc/out/start/goal, n/T/dt/radius out of
+ * range, bad enums, u_lo > u_hi; UNSUPPORTED for n > 32 or
+ * T * n * d_u > D4ORM_MAX_CTRL.  *out is NULL on error. */
+d4orm_status d4orm_problem_create(const d4orm_problem_desc *desc, d4orm_problem **out);
+
+/* Frees the handle and its device workspace (synchronises the device work
+ * the handle issued).  NULL is a no-op. */
+void d4orm_problem_destroy(d4orm_problem *problem);
+
+/* Rollout of one plan (Sec. IV-C; Algorithm 1 final line, Algorithm 2
+ * update): controls u_dev[T][n][d_u] are held to the control box and
+ * integrated from S.  states_dev (nullable) receives float[T+1][n][d_x].
+ * verdict_host (nullable) receives the Eq. (1)/(2) verdict with the reward
+ * weight of `params` (nullable: w_safe = 5); when it is given, the call
+ * synchronises `stream` before returning. */
+d4orm_status d4orm_rollout(d4orm_problem *problem, const d4orm_params *params, const float *u_dev,
+                           float *states_dev, d4orm_verdict *verdict_host, void *stream);
+
+/* One denoising step i (Algorithm 1 body, on deformations per Algorithm 2):
+ *   samples   dU_j = dU_i / sqrt(abar_i) + sqrt(1/abar_i - 1) eps_j  (Eq. (12))
+ *   fitness   r_j  = Eq. (3) of rollout(S, clip(u_base + dU_j))
+ *   weights   w_j  = softmax(zscore(r) / lambda)                     (Eq. (6))
+ *   update    dU_{i-1} = sqrt(abar_{i-1}) * sum_j w_j dU_j          (Eq. (13))
+ * eps_j is regenerated from Philox4x32-10 (never stored), indexed by
+ * (iter, step_i, j, robot, element): see d4orm_sample_noise.
+ * u_base_dev, du_in_dev: [T][n][d_u]; du_out_dev: [T][n][d_u] (must not
+ * alias du_in_dev); fitness_dev: nullable float[N] receiving r_j.
+ * Errors: INVALID_ARG for null pointers, step_i not in 1..K, iter not in
+ * 0..D4ORM_MAX_ITERS-1, bad params; OOM if the workspace cannot grow. */
+d4orm_status d4orm_denoise_step(d4orm_problem *problem, const d4orm_params *params, int iter, int step_i,
+                                const float *u_base_dev, const float *du_in_dev, float *du_out_dev,
+                                float *fitness_dev, void *stream);
+
+/* d4orm_denoise_step with a CUDA event recorded on `stream` between its
+ * kernels; synchronises and writes the device time of each kernel, in ms,
+ * to kernel_ms_host[4]: {rollout+fitness, softmax weights, weighted noise
+ * sum, finalize}.  Results are identical to d4orm_denoise_step. */
+d4orm_status d4orm_denoise_step_timed(d4orm_problem *problem, const d4orm_params *params, int iter, int step_i,
+                                      const float *u_base_dev, const float *du_in_dev, float *du_out_dev,
+                                      float *fitness_dev, float *kernel_ms_host, void *stream);
+
+/* Algorithm 2 with an anytime budget.  tau.u starts at zero.  Each
+ * iteration runs steps K..1 from dU_K = 0 (Sec. IV-D), or, in the first
+ * iteration when du_init_dev is given, steps start_step..1 from
+ * dU = du_init_dev; then tau.u <- clip(tau.u + dU_0) and the plan is rolled
+ * out and judged.  u_out_dev [T][n][d_u] receives the final tau.u;
+ * out_host (nullable) the result.  Synchronises `stream`.  Steps of one
+ * iteration are replayed from a CUDA graph cached in the handle. */
+d4orm_status d4orm_solve(d4orm_problem *problem, const d4orm_params *params, const d4orm_budget *budget,
+                         const float *du_init_dev, float *u_out_dev, d4orm_result *out_host, void *stream);
+
+/* The sample noise eps of Eq. (12) exactly as the step kernels regenerate
+ * it: eps_dev[count][T][n][d_u] for samples j0..j0+count-1 of (iter,
+ * step_i).  Element e = t*d_u + d of robot k's stream, quad q = e/4, takes
+ * word e%4 of Philox4x32-10 with counter (q, j, (k & 0xff) | (step_i << 8),
+ * iter | (tag << 12)) and key (seed lo, seed hi), through Box-Muller on
+ * word pairs (0,1) and (2,3).  Used by parity tests. */
+d4orm_status d4orm_sample_noise(d4orm_problem *problem, const d4orm_params *params, int iter, int step_i,
+                                int j0, int count, float *eps_dev, void *stream);
+
+/* Raw Philox4x32-10 (Salmon et al., SC'11): out_dev[i][0..3] =
+ * Philox(ctr_dev[i][0..3], key = (key0, key1)) for i < count. */
+d4orm_status d4orm_philox4x32_10(const uint32_t *ctr_dev, uint32_t key0, uint32_t key1, int count,
+                                 uint32_t *out_dev, void *stream);
+
+/* Static string for a status code. */
+const char *d4orm_status_string(d4orm_status status);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char *d4orm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* D4ORM_H */

@@ -106,7 +106,9 @@ def _load():
         lib.orc_verdict_of.argtypes = [P(_Problem), ctypes.c_double, d, P(_Verdict)]
         lib.orc_weights.argtypes = [ctypes.c_int, d, ctypes.c_double, d]
         lib.orc_sample_fitness.argtypes = [P(_Problem), P(_Params), ctypes.c_int, ctypes.c_int, d, d,
-                                           ctypes.c_int, i32, d, d]
+                                           ctypes.c_int, i32, d, d, ctypes.c_double, i32]
+        lib.orc_fragile.argtypes = [P(_Problem), d, ctypes.c_double]
+        lib.orc_fragile.restype = ctypes.c_int
         lib.orc_denoise_step.argtypes = [P(_Problem), P(_Params), ctypes.c_int, ctypes.c_int, d, d, d, d, d, d]
         lib.orc_weighted_update.argtypes = [P(_Problem), P(_Params), ctypes.c_int, ctypes.c_int, d, d, d]
         lib.orc_apply.argtypes = [P(_Problem), d, d, d]
@@ -279,8 +281,10 @@ def weights(r: np.ndarray, lam: float) -> np.ndarray:
     return w
 
 
-def sample_fitness(prob: Problem, params: Params, it: int, i: int, u_base, du_in, js):
-    """(fitness[len(js)], threshold_gap[len(js)]) for the listed samples."""
+def sample_fitness(prob: Problem, params: Params, it: int, i: int, u_base, du_in, js, delta: float = 0.0,
+                   with_fragile: bool = False):
+    """(fitness[len(js)], threshold_gap[len(js)]) for the listed samples, plus
+    the per-sample fragile robot-timestep counts when with_fragile."""
     lib = _load()
     pc, pp = prob.c(), params.c()
     u_base = np.ascontiguousarray(u_base, dtype=np.float64)
@@ -288,9 +292,18 @@ def sample_fitness(prob: Problem, params: Params, it: int, i: int, u_base, du_in
     js = np.ascontiguousarray(js, dtype=np.int32)
     f = np.zeros(len(js))
     g = np.zeros(len(js))
+    fr = np.zeros(len(js), dtype=np.int32)
     lib.orc_sample_fitness(ctypes.byref(pc), ctypes.byref(pp), it, i, _dp(u_base), _dp(du_in), len(js),
-                           js.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(f), _dp(g))
-    return f, g
+                           js.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(f), _dp(g), delta,
+                           fr.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) if with_fragile else None)
+    return (f, g, fr) if with_fragile else (f, g)
+
+
+def fragile(prob: Problem, states: np.ndarray, delta: float) -> int:
+    lib = _load()
+    pc = prob.c()
+    states = np.ascontiguousarray(states, dtype=np.float64)
+    return lib.orc_fragile(ctypes.byref(pc), _dp(states), delta)
 
 
 def denoise_step(prob: Problem, params: Params, it: int, i: int, u_base, du_in, fitness_in=None):

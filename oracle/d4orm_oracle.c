@@ -232,6 +232,31 @@ double orc_reward(const orc_problem *p, double w_safe, const double *states,
     return total / ((double)n * (double)T);
 }
 
+/* Fragility of the Eq. (5) indicator, for comparing a binary32 evaluation
+ * against this one: the number of robot-timesteps (t >= 1, k) at which some
+ * other robot's distance lies within delta of 2R_a + eps.  Only those
+ * indicators can differ between two evaluations whose pair distances agree
+ * to within delta; each such flip moves Eq. (3) by w / (nT). */
+int orc_fragile(const orc_problem *p, const double *states, double delta)
+{
+    int d_x, d_u, d_p;
+    orc_dims(p->dyn, &d_x, &d_u, &d_p);
+    const int n = p->n, T = p->T;
+    const double thr = 2.0 * p->radius + p->eps_margin;
+    int count = 0;
+    for (int t = 1; t <= T; ++t)
+        for (int k = 0; k < n; ++k) {
+            int fragile = 0;
+            for (int l = 0; l < n; ++l) {
+                if (l == k) continue;
+                double dkl = pos_dist(&states[((size_t)t * n + k) * d_x], &states[((size_t)t * n + l) * d_x], d_p);
+                if (fabs(dkl - thr) < delta) fragile = 1;
+            }
+            count += fragile;
+        }
+    return count;
+}
+
 /* Eq. (1) conditions and the Eq. (2) objective on a rolled-out plan.
  *   safety:   |p_k[t] - p_l[t]| > 2 R_a for all t in 0..T, k != l
  *   terminal: |p_k[T] - g_k| <= goal_tol for all k (positions only)
@@ -315,7 +340,8 @@ static void make_sample(const orc_problem *p, const orc_params *pp, int it, int 
  * base trajectory (Sec. IV-D), rolled out from S and scored by Eq. (3). */
 void orc_sample_fitness(const orc_problem *p, const orc_params *pp, int it, int i,
                         const double *u_base, const double *du_in,
-                        int count, const int *js, double *fitness, double *gap)
+                        int count, const int *js, double *fitness, double *gap,
+                        double delta, int *fragile)
 {
     int d_x, d_u, d_p;
     orc_dims(p->dyn, &d_x, &d_u, &d_p);
@@ -332,6 +358,7 @@ void orc_sample_fitness(const orc_problem *p, const orc_params *pp, int it, int 
         for (size_t e = 0; e < nu; ++e) ctrl[e] = u_base[e] + sample[e];
         orc_rollout(p, ctrl, states);
         fitness[c] = orc_reward(p, pp->w_safe, states, gap ? &gap[c] : NULL);
+        if (fragile) fragile[c] = orc_fragile(p, states, delta);
     }
     free(alpha); free(abar); free(sample); free(ctrl); free(states);
 }
@@ -376,7 +403,7 @@ void orc_denoise_step(const orc_problem *p, const orc_params *pp, int it, int i,
     } else {
         int *js = malloc(sizeof(int) * N);
         for (int j = 0; j < N; ++j) js[j] = j;
-        orc_sample_fitness(p, pp, it, i, u_base, du_in, N, js, r, gap);
+        orc_sample_fitness(p, pp, it, i, u_base, du_in, N, js, r, gap, 0.0, NULL);
         free(js);
     }
     if (fitness) memcpy(fitness, r, sizeof(double) * N);

@@ -99,9 +99,11 @@ void orc_verdict_of(const orc_problem *p, double w_safe, const double *states,
 void orc_weights(int N, const double *r, double lambda, double *w);
 
 /* One denoising step of Algorithm 1 applied to deformations (Algorithm 2). */
+int orc_fragile(const orc_problem *p, const double *states, double delta);
 void orc_sample_fitness(const orc_problem *p, const orc_params *pp, int it, int i,
                         const double *u_base, const double *du_in,
-                        int count, const int *js, double *fitness, double *gap);
+                        int count, const int *js, double *fitness, double *gap,
+                        double delta, int *fragile);
 void orc_denoise_step(const orc_problem *p, const orc_params *pp, int it, int i,
                       const double *u_base, const double *du_in, double *du_out,
                       double *fitness, const double *fitness_in, double *gap);

@@ -1,0 +1,308 @@
+"""Python binding of libd4orm.so, the GB300 (sm_103a) D4orm hot path.
+
+A thin ctypes layer over the C ABI in ``include/d4orm.h``: functions keep the
+C names and only marshal arguments (device pointers may be given as ints or
+as objects with ``data_ptr()``, e.g. torch tensors; streams as ints, None, or
+objects with ``cuda_stream``).  Every step of the denoising path runs in the
+library's CUDA kernels; there is no CPU fallback, and importing this package
+raises if the compiled library is missing.
+
+Paper: Zhang et al., "D4orm: Multi-Robot Trajectories with Dynamics-aware
+Diffusion Denoised Deformations" (IROS 2025) -- Eq. (1)-(13), Algorithms 1-2.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libd4orm.so")
+
+HOLO2D, HOLO3D, UNICYCLE, DIFFDRIVE4 = 0, 1, 2, 3
+EULER, RK4 = 0, 1
+DIMS = {HOLO2D: (4, 2, 2), HOLO3D: (6, 3, 3), UNICYCLE: (3, 2, 2), DIFFDRIVE4: (4, 2, 2)}
+MAX_ROBOTS = 32
+MAX_ITERS = 4096
+MAX_TAG = (1 << 20) - 1
+MAX_CTRL = 49152
+
+STATUS = {0: "D4ORM_OK", 1: "D4ORM_ERR_INVALID_ARG", 2: "D4ORM_ERR_UNSUPPORTED", 3: "D4ORM_ERR_OOM",
+          4: "D4ORM_ERR_CUDA", 5: "D4ORM_ERR_TIMEOUT", 6: "D4ORM_ERR_CANCELLED"}
+
+# Every entry point declared in include/d4orm.h.
+EXPORTS = (
+    "d4orm_problem_create", "d4orm_problem_destroy", "d4orm_rollout", "d4orm_denoise_step",
+    "d4orm_denoise_step_timed", "d4orm_solve",
+    "d4orm_sample_noise", "d4orm_philox4x32_10", "d4orm_status_string", "d4orm_last_error",
+)
+
+
+class D4ormError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [
+        ("n_robots", ctypes.c_int), ("T", ctypes.c_int), ("dyn", ctypes.c_int), ("integ", ctypes.c_int),
+        ("dt", ctypes.c_float), ("radius", ctypes.c_float), ("eps_margin", ctypes.c_float),
+        ("goal_tol", ctypes.c_float), ("v_max", ctypes.c_float),
+        ("start", ctypes.POINTER(ctypes.c_float)), ("goal", ctypes.POINTER(ctypes.c_float)),
+        ("u_lo", ctypes.POINTER(ctypes.c_float)), ("u_hi", ctypes.POINTER(ctypes.c_float)),
+    ]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("n_samples", ctypes.c_int), ("n_steps", ctypes.c_int), ("temperature", ctypes.c_float),
+        ("w_safe", ctypes.c_float), ("beta0", ctypes.c_float), ("beta1", ctypes.c_float),
+        ("seed", ctypes.c_uint64), ("instance_tag", ctypes.c_uint32),
+    ]
+
+
+class _Budget(ctypes.Structure):
+    _fields_ = [
+        ("max_iters", ctypes.c_int), ("deadline_ms", ctypes.c_double), ("stop_on_success", ctypes.c_int),
+        ("start_step", ctypes.c_int),
+    ]
+
+
+class _Verdict(ctypes.Structure):
+    _fields_ = [
+        ("collision_free", ctypes.c_int), ("goal_reached", ctypes.c_int), ("reward", ctypes.c_float),
+        ("objective", ctypes.c_float), ("min_pair_dist", ctypes.c_float),
+    ]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [
+        ("verdict", _Verdict), ("iters_run", ctypes.c_int), ("first_success_iter", ctypes.c_int),
+        ("ms_to_success", ctypes.c_double), ("ms_total", ctypes.c_double),
+    ]
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'` "
+            "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i, u32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32
+    lib.d4orm_problem_create.argtypes = [ctypes.POINTER(_Desc), ctypes.POINTER(vp)]
+    lib.d4orm_problem_create.restype = i
+    lib.d4orm_problem_destroy.argtypes = [vp]
+    lib.d4orm_problem_destroy.restype = None
+    lib.d4orm_rollout.argtypes = [vp, ctypes.POINTER(_Params), vp, vp, ctypes.POINTER(_Verdict), vp]
+    lib.d4orm_rollout.restype = i
+    lib.d4orm_denoise_step.argtypes = [vp, ctypes.POINTER(_Params), i, i, vp, vp, vp, vp, vp]
+    lib.d4orm_denoise_step.restype = i
+    lib.d4orm_denoise_step_timed.argtypes = [vp, ctypes.POINTER(_Params), i, i, vp, vp, vp, vp,
+                                             ctypes.POINTER(ctypes.c_float), vp]
+    lib.d4orm_denoise_step_timed.restype = i
+    lib.d4orm_solve.argtypes = [vp, ctypes.POINTER(_Params), ctypes.POINTER(_Budget), vp, vp,
+                                ctypes.POINTER(_Result), vp]
+    lib.d4orm_solve.restype = i
+    lib.d4orm_sample_noise.argtypes = [vp, ctypes.POINTER(_Params), i, i, i, i, vp, vp]
+    lib.d4orm_sample_noise.restype = i
+    lib.d4orm_philox4x32_10.argtypes = [vp, u32, u32, i, vp, vp]
+    lib.d4orm_philox4x32_10.restype = i
+    lib.d4orm_status_string.argtypes = [i]
+    lib.d4orm_status_string.restype = ctypes.c_char_p
+    lib.d4orm_last_error.argtypes = []
+    lib.d4orm_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+lib = _load()
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        raise D4ormError(status, lib.d4orm_last_error().decode())
+
+
+def _ptr(x) -> ctypes.c_void_p | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    raise TypeError(f"cannot take a device pointer from {type(x)!r}")
+
+
+def _stream(s) -> ctypes.c_void_p | None:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return ctypes.c_void_p(s)
+    if hasattr(s, "cuda_stream"):
+        return ctypes.c_void_p(s.cuda_stream)
+    raise TypeError(f"cannot take a stream handle from {type(s)!r}")
+
+
+def _fbuf(values, count: int):
+    vals = [float(v) for v in values]
+    if len(vals) != count:
+        raise ValueError(f"expected {count} values, got {len(vals)}")
+    return (ctypes.c_float * count)(*vals)
+
+
+@dataclass
+class Params:
+    """Denoising parameters (d4orm_params)."""
+    n_samples: int
+    n_steps: int = 100
+    temperature: float = 0.1
+    w_safe: float = 5.0
+    beta0: float = 1e-4
+    beta1: float = 1e-2
+    seed: int = 0
+    instance_tag: int = 0
+
+    def c(self) -> _Params:
+        return _Params(self.n_samples, self.n_steps, self.temperature, self.w_safe, self.beta0, self.beta1,
+                       self.seed, self.instance_tag)
+
+
+@dataclass
+class Budget:
+    """Anytime budget (d4orm_budget)."""
+    max_iters: int = 1
+    deadline_ms: float = 0.0
+    stop_on_success: bool = False
+    start_step: int = 0
+
+    def c(self) -> _Budget:
+        return _Budget(self.max_iters, self.deadline_ms, int(self.stop_on_success), self.start_step)
+
+
+def _verdict(v: _Verdict) -> dict:
+    return dict(collision_free=bool(v.collision_free), goal_reached=bool(v.goal_reached), reward=v.reward,
+                objective=v.objective, min_pair_dist=v.min_pair_dist)
+
+
+def d4orm_problem_create(n_robots: int, T: int, dyn: int, integ: int, dt: float, radius: float, start, goal,
+                         eps_margin: float = 0.05, goal_tol: float = 0.1, v_max: float = 0.0,
+                         u_lo=None, u_hi=None) -> ctypes.c_void_p:
+    """Create a problem handle; start/goal are host sequences of n*d_x floats."""
+    d_x, d_u, _ = DIMS.get(dyn, (4, 2, 2))
+    flat_s = [float(v) for v in _flatten(start)]
+    flat_g = [float(v) for v in _flatten(goal)]
+    s = (ctypes.c_float * max(1, len(flat_s)))(*flat_s)
+    g = (ctypes.c_float * max(1, len(flat_g)))(*flat_g)
+    if n_robots >= 1 and (len(flat_s) != n_robots * d_x or len(flat_g) != n_robots * d_x):
+        raise ValueError("start/goal must hold n_robots * d_x values")
+    lo = _fbuf(u_lo, d_u) if u_lo is not None else None
+    hi = _fbuf(u_hi, d_u) if u_hi is not None else None
+    desc = _Desc(n_robots, T, dyn, integ, dt, radius, eps_margin, goal_tol, v_max, s, g,
+                 ctypes.cast(lo, ctypes.POINTER(ctypes.c_float)) if lo is not None else None,
+                 ctypes.cast(hi, ctypes.POINTER(ctypes.c_float)) if hi is not None else None)
+    h = ctypes.c_void_p()
+    _check(lib.d4orm_problem_create(ctypes.byref(desc), ctypes.byref(h)))
+    return h
+
+
+def d4orm_problem_destroy(handle) -> None:
+    lib.d4orm_problem_destroy(handle)
+
+
+def d4orm_rollout(handle, params: Params | None, u_dev, states_dev=None, want_verdict: bool = True, stream=None):
+    v = _Verdict()
+    pc = params.c() if params is not None else None
+    _check(lib.d4orm_rollout(handle, ctypes.byref(pc) if pc is not None else None, _ptr(u_dev), _ptr(states_dev),
+                             ctypes.byref(v) if want_verdict else None, _stream(stream)))
+    return _verdict(v) if want_verdict else None
+
+
+def d4orm_denoise_step(handle, params: Params, iter: int, step_i: int, u_base_dev, du_in_dev, du_out_dev,
+                       fitness_dev=None, stream=None) -> None:
+    pc = params.c()
+    _check(lib.d4orm_denoise_step(handle, ctypes.byref(pc), iter, step_i, _ptr(u_base_dev), _ptr(du_in_dev),
+                                  _ptr(du_out_dev), _ptr(fitness_dev), _stream(stream)))
+
+
+def d4orm_denoise_step_timed(handle, params: Params, iter: int, step_i: int, u_base_dev, du_in_dev, du_out_dev,
+                             fitness_dev=None, stream=None) -> list[float]:
+    """Same as d4orm_denoise_step; returns the per-kernel device times [ms]
+    (rollout+fitness, softmax weights, weighted noise sum, finalize)."""
+    pc = params.c()
+    ms = (ctypes.c_float * 4)()
+    _check(lib.d4orm_denoise_step_timed(handle, ctypes.byref(pc), iter, step_i, _ptr(u_base_dev), _ptr(du_in_dev),
+                                        _ptr(du_out_dev), _ptr(fitness_dev), ms, _stream(stream)))
+    return list(ms)
+
+
+def d4orm_solve(handle, params: Params, budget: Budget, u_out_dev, du_init_dev=None, stream=None) -> dict:
+    pc, bc = params.c(), budget.c()
+    r = _Result()
+    _check(lib.d4orm_solve(handle, ctypes.byref(pc), ctypes.byref(bc), _ptr(du_init_dev), _ptr(u_out_dev),
+                           ctypes.byref(r), _stream(stream)))
+    return dict(verdict=_verdict(r.verdict), iters_run=r.iters_run, first_success_iter=r.first_success_iter,
+                ms_to_success=r.ms_to_success, ms_total=r.ms_total)
+
+
+def d4orm_sample_noise(handle, params: Params, iter: int, step_i: int, j0: int, count: int, eps_dev,
+                       stream=None) -> None:
+    pc = params.c()
+    _check(lib.d4orm_sample_noise(handle, ctypes.byref(pc), iter, step_i, j0, count, _ptr(eps_dev),
+                                  _stream(stream)))
+
+
+def d4orm_philox4x32_10(ctr_dev, key0: int, key1: int, count: int, out_dev, stream=None) -> None:
+    _check(lib.d4orm_philox4x32_10(_ptr(ctr_dev), key0 & 0xFFFFFFFF, key1 & 0xFFFFFFFF, count, _ptr(out_dev),
+                                   _stream(stream)))
+
+
+def d4orm_status_string(status: int) -> str:
+    return lib.d4orm_status_string(status).decode()
+
+
+def d4orm_last_error() -> str:
+    return lib.d4orm_last_error().decode()
+
+
+def _flatten(x):
+    if hasattr(x, "ravel"):
+        return list(x.ravel())
+    out = []
+    for v in x:
+        if isinstance(v, (list, tuple)) or hasattr(v, "__len__"):
+            out.extend(_flatten(v))
+        else:
+            out.append(v)
+    return out
+
+
+class Problem:
+    """Owning wrapper of a d4orm_problem handle built from a scenario-like
+    object (fields n, T, dyn, integ, dt, radius, start, goal, u_lo, u_hi,
+    v_max, eps_margin, goal_tol)."""
+
+    def __init__(self, inst):
+        self.inst = inst
+        self.n, self.T, self.dyn = inst.n, inst.T, inst.dyn
+        self.d_x, self.d_u, self.d_p = DIMS[inst.dyn]
+        self.handle = d4orm_problem_create(inst.n, inst.T, inst.dyn, inst.integ, inst.dt, inst.radius,
+                                           inst.start, inst.goal, eps_margin=inst.eps_margin,
+                                           goal_tol=inst.goal_tol, v_max=inst.v_max, u_lo=inst.u_lo,
+                                           u_hi=inst.u_hi)
+
+    def close(self):
+        if self.handle:
+            d4orm_problem_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

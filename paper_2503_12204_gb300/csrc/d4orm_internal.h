@@ -1,0 +1,53 @@
+// d4orm_internal.h -- launchers shared by the C-ABI layer and the kernel
+// translation units (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "d4orm.h"
+#include "d4orm_device.cuh"
+
+namespace d4orm {
+
+// Split of the weighted noise sum over samples: `chunks` partial sums of
+// `chunk` samples each (chunk a multiple of 8).
+struct SumSplit {
+    int chunks;
+    int chunk;
+};
+SumSplit plan_weighted_sum(const DevProblem& P, int N, int sm_count);
+
+// Kernel attributes K2 needs for problem P (call outside stream capture).
+cudaError_t prepare_rollout_fitness(const DevProblem& P);
+
+// K2: fused sample rollout + fitness (Eq. (12) samples, Eq. (1) rollout,
+// Eq. (3)-(5) reward).  fitness[N].
+cudaError_t launch_rollout_fitness(const DevProblem& P, const DevStep& S, const float* u_base,
+                                   const float* du_in, float* fitness, const int* it_dev, cudaStream_t st);
+
+// K3a: batch z-score + softmax (Sec. IV-C, Eq. (6)).  w[N] (normalised).
+cudaError_t launch_softmax_weights(const float* fitness, int N, float inv_lambda, float* w, float* stats,
+                                   cudaStream_t st);
+
+// K3b: partial[c][n*Q][4] = sum over samples j of chunk c of w_j eps_j.
+cudaError_t launch_weighted_sum(const DevProblem& P, const DevStep& S, const float* w, SumSplit split,
+                                float* partial, const int* it_dev, cudaStream_t st);
+
+// K3c: du_out = g (c du_in + sigma sum_c partial[c])  (Eq. (13)).
+cudaError_t launch_finalize(const DevProblem& P, const DevStep& S, const float* partial, SumSplit split,
+                            const float* du_in, float* du_out, cudaStream_t st);
+
+// K4: u_out = clip(u_base + du0) (du0 nullable), rollout, verdict.
+// states (nullable) [T+1][n][d_x]; verdict (nullable) device struct;
+// it_inc (nullable) incremented once when done.
+cudaError_t launch_apply_rollout_verdict(const DevProblem& P, float w_safe, const float* u_base, const float* du0,
+                                         float* u_out, float* states, d4orm_verdict* verdict, int* it_inc,
+                                         cudaStream_t st);
+
+// Diagnostics: regenerated noise and raw Philox.
+cudaError_t launch_sample_noise(const DevProblem& P, const DevStep& S, int j0, int count, float* eps,
+                                cudaStream_t st);
+cudaError_t launch_philox(const uint32_t* ctr, uint32_t key0, uint32_t key1, int count, uint32_t* out,
+                          cudaStream_t st);
+
+}  // namespace d4orm

@@ -1,0 +1,168 @@
+// k_rollout_fitness.cu -- K2, the fused sample rollout + fitness kernel.
+//
+// One denoising step evaluates N deformation samples (Eq. (12), Algorithm 1
+// sampling + rollout lines).  Each sample is one whole robot team, rolled
+// out over T steps and scored by the team reward of Eq. (3)-(5):
+//
+//   u_{t,k}  = clip(M_{t,k} + sigma_i eps_{j,t,k}),  M = u_base + c_i dU_i
+//   x_{t+1}  = integrate(x_t, u_t)                    (Sec. III Eq. (1), Sec. V)
+//   r_j      = 1/(nT) sum_{t=1..T} sum_k [1 - |p_k - g_k| / d0_k
+//                                         - w Ind(exists l: |p_k - p_l| <= 2R+eps)]
+//
+// Mapping: robots in lanes.  A warp holds 32/SEG samples, one per aligned
+// segment of SEG lanes (SEG = next power of two >= n); the robot state lives
+// in registers for the whole horizon.  Pairwise distances of Eq. (5) are
+// read from the partner lanes with butterfly shuffles inside the segment,
+// and the per-sample fitness is reduced with segment shuffles: nothing but
+// the final float per sample leaves the SM.  The mean controls M are staged
+// once per CTA in shared memory.  The noise eps is regenerated from Philox in
+// registers, four time steps at a time (d_u Philox calls), never stored.
+#include <cmath>
+
+#include "d4orm_internal.h"
+
+namespace d4orm {
+
+constexpr int kK2Threads = 256;
+
+template <int DYN, int SEG>
+__global__ void __launch_bounds__(kK2Threads)
+k_rollout_fitness(const DevProblem P, const DevStep S, const float* __restrict__ u_base,
+                  const float* __restrict__ du_in, float* __restrict__ fitness, const int* __restrict__ it_dev)
+{
+    using D = DynDims<DYN>;
+    constexpr int DX = D::DX, DU = D::DU, DP = D::DP;
+    constexpr int SPW = 32 / SEG;  // samples per warp
+    extern __shared__ float sM[];  // M[t][k][d]
+
+    const int nctrl = P.T * P.n * DU;
+    for (int e = threadIdx.x; e < nctrl; e += blockDim.x) sM[e] = fmaf(S.c, du_in[e], u_base[e]);
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int k = lane & (SEG - 1);
+    const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int j = warp * SPW + lane / SEG;
+    const bool robot = k < P.n;
+    const int kr = robot ? k : P.n - 1;
+    const uint32_t c3 = iter_word(S, it_dev);
+
+    float x[DX];
+    load_start<DYN>(x, P, k);
+    float g[DP];
+#pragma unroll
+    for (int d = 0; d < DP; ++d) g[d] = P.goal[kr * 3 + d];
+    const float inv_d0 = P.inv_d0[kr];
+    const float w_safe = S.w_safe;
+    const int rowM = P.n * DU;
+    const float* Mk = sM + kr * DU;
+    float acc = 0.0f;
+
+    for (int t0 = 0; t0 < P.T; t0 += 4) {
+        float eps[4 * DU];
+        const uint32_t q0 = (uint32_t)(t0 * DU) >> 2;
+#pragma unroll
+        for (int c = 0; c < DU; ++c) noise_quad(S, c3, q0 + c, (uint32_t)j, (uint32_t)k, &eps[4 * c]);
+#pragma unroll
+        for (int tt = 0; tt < 4; ++tt) {
+            const int t = t0 + tt;
+            if (t < P.T) {  // uniform across the warp
+                float u[DU];
+#pragma unroll
+                for (int d = 0; d < DU; ++d)
+                    u[d] = clampf(fmaf(S.sigma, eps[tt * DU + d], Mk[t * rowM + d]), P.u_lo[d], P.u_hi[d]);
+                integrate<DYN>(x, u, P);
+                // Eq. (4): goal term
+                float dg2 = 0.0f;
+#pragma unroll
+                for (int d = 0; d < DP; ++d) {
+                    const float e = x[d] - g[d];
+                    dg2 = fmaf(e, e, dg2);
+                }
+                // Eq. (5): any partner inside 2R+eps (squared distances)
+                bool hit = false;
+#pragma unroll
+                for (int s = 1; s < SEG; ++s) {
+                    float d2 = 0.0f;
+#pragma unroll
+                    for (int d = 0; d < DP; ++d) {
+                        const float e = x[d] - __shfl_xor_sync(kFull, x[d], s);
+                        d2 = fmaf(e, e, d2);
+                    }
+                    hit |= ((k ^ s) < P.n) & (d2 <= P.thr2);
+                }
+                if (robot) acc += (1.0f - sqrtf(dg2) * inv_d0) - (hit ? w_safe : 0.0f);
+            }
+        }
+    }
+    acc = seg_sum<SEG>(acc);
+    if (k == 0 && j < S.N) fitness[j] = acc * P.inv_nT;
+}
+
+// Opt in to up to 200 KB of dynamic shared memory (mean controls of the
+// largest problems).  Called outside any stream capture.
+template <int DYN, int SEG>
+static cudaError_t prepare_k2()
+{
+    return cudaFuncSetAttribute(k_rollout_fitness<DYN, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                200 * 1024);
+}
+
+template <int DYN>
+static cudaError_t prepare_dyn(int n)
+{
+    if (n <= 1) return prepare_k2<DYN, 1>();
+    if (n <= 2) return prepare_k2<DYN, 2>();
+    if (n <= 4) return prepare_k2<DYN, 4>();
+    if (n <= 8) return prepare_k2<DYN, 8>();
+    if (n <= 16) return prepare_k2<DYN, 16>();
+    return prepare_k2<DYN, 32>();
+}
+
+cudaError_t prepare_rollout_fitness(const DevProblem& P)
+{
+    switch (P.dyn) {
+    case HOLO2D: return prepare_dyn<HOLO2D>(P.n);
+    case HOLO3D: return prepare_dyn<HOLO3D>(P.n);
+    case UNICYCLE: return prepare_dyn<UNICYCLE>(P.n);
+    case DIFFDRIVE4: return prepare_dyn<DIFFDRIVE4>(P.n);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int DYN, int SEG>
+static cudaError_t launch_k2(const DevProblem& P, const DevStep& S, const float* u_base, const float* du_in,
+                             float* fitness, const int* it_dev, cudaStream_t st)
+{
+    constexpr int spb = (kK2Threads / 32) * (32 / SEG);
+    const size_t smem = (size_t)P.T * P.n * DynDims<DYN>::DU * sizeof(float);
+    const int grid = (S.N + spb - 1) / spb;
+    k_rollout_fitness<DYN, SEG><<<grid, kK2Threads, smem, st>>>(P, S, u_base, du_in, fitness, it_dev);
+    return cudaGetLastError();
+}
+
+template <int DYN>
+static cudaError_t dispatch_seg(const DevProblem& P, const DevStep& S, const float* u_base, const float* du_in,
+                                float* fitness, const int* it_dev, cudaStream_t st)
+{
+    if (P.n <= 1) return launch_k2<DYN, 1>(P, S, u_base, du_in, fitness, it_dev, st);
+    if (P.n <= 2) return launch_k2<DYN, 2>(P, S, u_base, du_in, fitness, it_dev, st);
+    if (P.n <= 4) return launch_k2<DYN, 4>(P, S, u_base, du_in, fitness, it_dev, st);
+    if (P.n <= 8) return launch_k2<DYN, 8>(P, S, u_base, du_in, fitness, it_dev, st);
+    if (P.n <= 16) return launch_k2<DYN, 16>(P, S, u_base, du_in, fitness, it_dev, st);
+    return launch_k2<DYN, 32>(P, S, u_base, du_in, fitness, it_dev, st);
+}
+
+cudaError_t launch_rollout_fitness(const DevProblem& P, const DevStep& S, const float* u_base, const float* du_in,
+                                   float* fitness, const int* it_dev, cudaStream_t st)
+{
+    switch (P.dyn) {
+    case HOLO2D: return dispatch_seg<HOLO2D>(P, S, u_base, du_in, fitness, it_dev, st);
+    case HOLO3D: return dispatch_seg<HOLO3D>(P, S, u_base, du_in, fitness, it_dev, st);
+    case UNICYCLE: return dispatch_seg<UNICYCLE>(P, S, u_base, du_in, fitness, it_dev, st);
+    case DIFFDRIVE4: return dispatch_seg<DIFFDRIVE4>(P, S, u_base, du_in, fitness, it_dev, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace d4orm

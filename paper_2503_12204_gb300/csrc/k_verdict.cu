@@ -1,0 +1,192 @@
+// k_verdict.cu -- K4 (iteration end of Algorithm 2: apply the deformation,
+// roll the plan out, judge it) and the noise diagnostics kernels.
+//
+// K4 runs one warp, robots in lanes:
+//   u      = clip(u_base + dU_0)                        (Algorithm 2 update)
+//   x      = rollout(S, u)                              (Sec. III Eq. (1))
+//   reward = Eq. (3); objective = Eq. (2) with |p - g| <= goal_tol;
+//   collision_free = |p_k - p_l| > 2 R_a for every t in 0..T (Eq. (1) safety);
+//   goal_reached   = |p_k[T] - g_k| <= goal_tol for every k (terminal condition).
+// It uses the same integrate<DYN> as K2, so d4orm_rollout's states are the
+// states every sample rollout computes.
+#include <cmath>
+
+#include "d4orm_internal.h"
+
+namespace d4orm {
+
+template <int DYN>
+__global__ void __launch_bounds__(32)
+k_apply_rollout_verdict(const DevProblem P, float w_safe, const float* u_base, const float* du0, float* u_out,
+                        float* __restrict__ states, d4orm_verdict* __restrict__ verdict, int* it_inc)
+{
+    using D = DynDims<DYN>;
+    constexpr int DX = D::DX, DU = D::DU, DP = D::DP;
+    const int k = threadIdx.x;
+    const bool robot = k < P.n;
+    const int kr = robot ? k : P.n - 1;
+    float x[DX];
+    load_start<DYN>(x, P, k);
+    float g[DP];
+#pragma unroll
+    for (int d = 0; d < DP; ++d) g[d] = P.goal[kr * 3 + d];
+    const float inv_d0 = P.inv_d0[kr];
+
+    auto pair_min = [&](float cur) {
+        float m = cur;
+        for (int s = 1; s < 32; ++s) {
+            float d2 = 0.0f;
+#pragma unroll
+            for (int d = 0; d < DP; ++d) {
+                const float e = x[d] - __shfl_xor_sync(kFull, x[d], s);
+                d2 = fmaf(e, e, d2);
+            }
+            if (((k ^ s) < P.n) && robot) m = fminf(m, d2);
+        }
+        return m;
+    };
+    if (states && robot)
+        for (int c = 0; c < DX; ++c) states[(size_t)k * DX + c] = x[c];
+    float min_d2 = pair_min(INFINITY);
+    float acc = 0.0f;
+    int at_goal = 0;
+    float dg2 = 0.0f;
+    for (int t = 0; t < P.T; ++t) {
+        float u[DU];
+#pragma unroll
+        for (int d = 0; d < DU; ++d) {
+            const size_t idx = ((size_t)t * P.n + kr) * DU + d;
+            const float v = clampf(u_base[idx] + (du0 ? du0[idx] : 0.0f), P.u_lo[d], P.u_hi[d]);
+            u[d] = v;
+            if (u_out && robot) u_out[idx] = v;
+        }
+        integrate<DYN>(x, u, P);
+        if (states && robot)
+            for (int c = 0; c < DX; ++c) states[((size_t)(t + 1) * P.n + k) * DX + c] = x[c];
+        dg2 = 0.0f;
+#pragma unroll
+        for (int d = 0; d < DP; ++d) {
+            const float e = x[d] - g[d];
+            dg2 = fmaf(e, e, dg2);
+        }
+        bool hit = false;
+        float m = INFINITY;
+        for (int s = 1; s < 32; ++s) {
+            float d2 = 0.0f;
+#pragma unroll
+            for (int d = 0; d < DP; ++d) {
+                const float e = x[d] - __shfl_xor_sync(kFull, x[d], s);
+                d2 = fmaf(e, e, d2);
+            }
+            if ((k ^ s) < P.n) {
+                hit |= d2 <= P.thr2;
+                m = fminf(m, d2);
+            }
+        }
+        if (robot) {
+            min_d2 = fminf(min_d2, m);
+            acc += (1.0f - sqrtf(dg2) * inv_d0) - (hit ? w_safe : 0.0f);
+            at_goal += dg2 <= P.tol2 ? 1 : 0;
+        }
+    }
+    int reached = (!robot || dg2 <= P.tol2) ? 1 : 0;
+    float acc_s = acc;
+    int goal_s = at_goal;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        acc_s += __shfl_xor_sync(kFull, acc_s, off);
+        goal_s += __shfl_xor_sync(kFull, goal_s, off);
+        min_d2 = fminf(min_d2, __shfl_xor_sync(kFull, min_d2, off));
+        reached &= __shfl_xor_sync(kFull, reached, off);
+    }
+    if (k == 0) {
+        if (verdict) {
+            d4orm_verdict v;
+            v.collision_free = (P.n < 2 || min_d2 > P.safe2) ? 1 : 0;
+            v.goal_reached = reached;
+            v.reward = acc_s * P.inv_nT;
+            v.objective = (float)goal_s * P.inv_nT;
+            v.min_pair_dist = P.n < 2 ? 1e30f : sqrtf(min_d2);
+            *verdict = v;
+        }
+        if (it_inc) *it_inc += 1;
+    }
+}
+
+cudaError_t launch_apply_rollout_verdict(const DevProblem& P, float w_safe, const float* u_base, const float* du0,
+                                         float* u_out, float* states, d4orm_verdict* verdict, int* it_inc,
+                                         cudaStream_t st)
+{
+    switch (P.dyn) {
+    case HOLO2D:
+        k_apply_rollout_verdict<HOLO2D><<<1, 32, 0, st>>>(P, w_safe, u_base, du0, u_out, states, verdict, it_inc);
+        break;
+    case HOLO3D:
+        k_apply_rollout_verdict<HOLO3D><<<1, 32, 0, st>>>(P, w_safe, u_base, du0, u_out, states, verdict, it_inc);
+        break;
+    case UNICYCLE:
+        k_apply_rollout_verdict<UNICYCLE><<<1, 32, 0, st>>>(P, w_safe, u_base, du0, u_out, states, verdict, it_inc);
+        break;
+    case DIFFDRIVE4:
+        k_apply_rollout_verdict<DIFFDRIVE4><<<1, 32, 0, st>>>(P, w_safe, u_base, du0, u_out, states, verdict,
+                                                              it_inc);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// eps[s][t][k][d] for samples j0 + s, s < count: one thread per (s, k, quad).
+__global__ void k_sample_noise(const DevProblem P, const DevStep S, int j0, int count, float* __restrict__ eps)
+{
+    const long long total = (long long)count * P.n * P.Q;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int s = (int)(idx / ((long long)P.n * P.Q));
+    const int rem = (int)(idx - (long long)s * P.n * P.Q);
+    const int k = rem / P.Q;
+    const int q = rem - k * P.Q;
+    float z[4];
+    noise_quad(S, iter_word(S, nullptr), (uint32_t)q, (uint32_t)(j0 + s), (uint32_t)k, z);
+    const int len = P.T * P.d_u;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int e = 4 * q + r;
+        if (e < len) {
+            const int t = e / P.d_u, d = e - t * P.d_u;
+            eps[(((size_t)s * P.T + t) * P.n + k) * P.d_u + d] = z[r];
+        }
+    }
+}
+
+__global__ void k_philox(const uint4* __restrict__ ctr, uint32_t key0, uint32_t key1, int count,
+                         uint4* __restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const uint4 c = ctr[i];
+    const U4 r = philox4x32_10(U4{c.x, c.y, c.z, c.w}, key0, key1);
+    out[i] = make_uint4(r.x, r.y, r.z, r.w);
+}
+
+cudaError_t launch_sample_noise(const DevProblem& P, const DevStep& S, int j0, int count, float* eps,
+                                cudaStream_t st)
+{
+    const long long total = (long long)count * P.n * P.Q;
+    if (total == 0) return cudaSuccess;
+    const int threads = 256;
+    const long long blocks = (total + threads - 1) / threads;
+    k_sample_noise<<<(unsigned)blocks, threads, 0, st>>>(P, S, j0, count, eps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox(const uint32_t* ctr, uint32_t key0, uint32_t key1, int count, uint32_t* out,
+                          cudaStream_t st)
+{
+    if (count == 0) return cudaSuccess;
+    k_philox<<<(count + 255) / 256, 256, 0, st>>>(reinterpret_cast<const uint4*>(ctr), key0, key1, count,
+                                                  reinterpret_cast<uint4*>(out));
+    return cudaGetLastError();
+}
+
+}  // namespace d4orm

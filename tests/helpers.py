@@ -1,0 +1,64 @@
+"""Test helpers: build the oracle's and the CUDA library's views of one
+seeded scenario from identical (binary32-rounded) inputs."""
+from __future__ import annotations
+
+import copy
+import importlib.util
+import os
+
+import numpy as np
+
+import scenarios
+
+
+def f32(x):
+    return float(np.float32(x))
+
+
+def round_instance(inst: scenarios.Instance) -> scenarios.Instance:
+    """Round every real input to binary32 so that both implementations see
+    exactly the same problem (the CUDA path takes float inputs)."""
+    r = copy.deepcopy(inst)
+    r.start = inst.start.astype(np.float32).astype(np.float64)
+    r.goal = inst.goal.astype(np.float32).astype(np.float64)
+    for name in ("dt", "radius", "v_max", "lam", "w_safe", "eps_margin", "goal_tol", "beta0", "beta1"):
+        setattr(r, name, f32(getattr(inst, name)))
+    r.u_lo = tuple(f32(v) for v in inst.u_lo)
+    r.u_hi = tuple(f32(v) for v in inst.u_hi)
+    return r
+
+
+def oracle_problem(o, inst: scenarios.Instance):
+    return o.Problem(n=inst.n, T=inst.T, dyn=inst.dyn, integ=inst.integ, dt=inst.dt, radius=inst.radius,
+                     start=inst.start, goal=inst.goal, u_lo=inst.u_lo, u_hi=inst.u_hi,
+                     eps_margin=inst.eps_margin, goal_tol=inst.goal_tol, v_max=inst.v_max)
+
+
+def oracle_params(o, inst: scenarios.Instance, N: int | None = None):
+    return o.Params(N=N or inst.N, K=inst.K, lam=inst.lam, w_safe=inst.w_safe, beta0=inst.beta0,
+                    beta1=inst.beta1, seed=inst.seed, tag=inst.tag)
+
+
+def gpu_params(g, inst: scenarios.Instance, N: int | None = None):
+    return g.Params(n_samples=N or inst.N, n_steps=inst.K, temperature=inst.lam, w_safe=inst.w_safe,
+                    beta0=inst.beta0, beta1=inst.beta1, seed=inst.seed, instance_tag=inst.tag)
+
+
+def small_instance(dyn: int, n: int, T: int, N: int, integ: int = scenarios.RK4, seed: int = 0,
+                   K: int = 20, layout_seed: int = 7, tag: int = 0) -> scenarios.Instance:
+    """A random box instance of the requested size (for parity cases)."""
+    rng = np.random.default_rng(layout_seed)
+    inst = scenarios.box_instance(rng, dyn, n, T, N, side=4.0 + n * 0.5, min_sep=0.6, K=K, seed=seed, tag=tag)
+    inst.integ = integ
+    return round_instance(inst)
+
+
+def build_library() -> None:
+    """Compile libd4orm.so if it is missing or stale (the build script is
+    loaded by path: importing the package loads the library)."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("d4orm_build", os.path.join(root, "paper_2503_12204_gb300",
+                                                                               "_build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod.build()

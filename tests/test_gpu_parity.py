@@ -1,0 +1,304 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs and the same Philox noise.
+
+Tolerances (FP32 path vs FP64 oracle):
+* Philox words: bit-exact.
+* eps: |d| <= 2e-6 |eps| + 1e-9 (a few binary32 ulp of accurate log/sqrt/sincospi).
+* rollout states: <= 1e-4 absolute (metres, m/s, rad).
+* per-sample fitness: |d| <= 1e-3 |r| + 1e-5, plus w/(nT) per fragile
+  robot-timestep -- one whose Eq. (5) indicator sits within 2e-4 m of its
+  threshold, where FP32 and FP64 positions may fall on different sides (each
+  flip moves Eq. (3) by exactly w/(nT)).  Fragile samples are counted.
+* weighted-mean update: max-norm difference <= 1e-3 ||dU||_inf + 1e-6 ||dU||_inf,
+  with the oracle's Eq. (6)/(12)/(13) run on the GPU's own fitness vector
+  (stage isolation), and again on the oracle's own fitness when no sample is
+  fragile.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import scenarios
+from helpers import gpu_params, oracle_params, oracle_problem, round_instance, small_instance
+
+pytestmark = pytest.mark.gpu
+
+DELTA = 2e-4
+
+
+@pytest.fixture(scope="module")
+def torch():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("CUDA device required")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def g(torch):
+    from helpers import build_library
+    build_library()
+    import paper_2503_12204_gb300 as g
+    return g
+
+
+def dev(torch, a, dtype=None):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype or torch.float32, device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+# ----------------------------------------------------------------------------- noise
+
+def test_philox_bit_exact(torch, g, oracle_lib):
+    rng = np.random.default_rng(123)
+    ctr = rng.integers(0, 2**32, size=(2048, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:4] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [1, 2, 3, 4], [0xFFFFFFFF, 0, 0xFFFFFFFF, 0]]
+    key = (0x9E3779B9, 0xDEADBEEF)
+    c_dev = torch.as_tensor(ctr.view(np.int32), device="cuda")
+    out = torch.zeros_like(c_dev)
+    g.d4orm_philox4x32_10(c_dev, key[0], key[1], len(ctr), out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(np.uint32)
+    for i in range(len(ctr)):
+        assert np.array_equal(got[i], oracle_lib.philox4x32_10(ctr[i], key)), i
+
+
+@pytest.mark.parametrize("dyn,n,T", [(0, 3, 13), (1, 5, 7), (2, 8, 10), (3, 1, 9)])
+def test_sample_noise_matches_oracle(torch, g, oracle_lib, dyn, n, T):
+    inst = small_instance(dyn, n, T, N=16, seed=0xABCDEF0123, tag=77)
+    prob = g.Problem(inst)
+    p = gpu_params(g, inst)
+    op = oracle_params(oracle_lib, inst)
+    j0, count, it, i = 5, 6, 3, 11
+    eps = torch.zeros((count, T, n, inst.dims[1]), device="cuda")
+    g.d4orm_sample_noise(prob.handle, p, it, i, j0, count, eps)
+    torch.cuda.synchronize()
+    got = host(eps)
+    for s in range(count):
+        want = oracle_lib.noise_block(oracle_problem(oracle_lib, inst), op, it, i, j0 + s)
+        err = np.abs(got[s] - want)
+        assert (err <= 2e-6 * np.abs(want) + 1e-9).all(), err.max()
+
+
+# ----------------------------------------------------------------------------- rollout
+
+ROLLOUT_CASES = [(0, 0, 4, 50), (0, 1, 5, 37), (1, 1, 16, 100), (1, 0, 3, 11), (2, 1, 8, 100), (2, 0, 6, 23),
+                 (3, 1, 7, 41), (3, 0, 2, 5), (0, 1, 32, 20), (2, 1, 1, 1)]
+
+
+@pytest.mark.parametrize("dyn,integ,n,T", ROLLOUT_CASES)
+def test_rollout_states_and_verdict(torch, g, oracle_lib, dyn, integ, n, T):
+    inst = small_instance(dyn, n, T, N=8, integ=integ)
+    rng = np.random.default_rng(n * 100 + T)
+    u = scenarios.random_controls(rng, inst, scale=1.4).astype(np.float32)  # some outside the box
+    prob = g.Problem(inst)
+    states = torch.zeros((T + 1, n, inst.dims[0]), device="cuda")
+    v = g.d4orm_rollout(prob.handle, gpu_params(g, inst), dev(torch, u), states)
+    op = oracle_problem(oracle_lib, inst)
+    want = oracle_lib.rollout(op, u.astype(np.float64))
+    got = host(states)
+    assert np.abs(got - want).max() <= 1e-4, np.abs(got - want).max()
+    vo = oracle_lib.verdict(op, inst.w_safe, want)
+    if abs(vo["min_pair_dist"] - 2 * inst.radius) > DELTA:
+        assert v["collision_free"] == vo["collision_free"]
+    final = np.linalg.norm(want[-1, :, :inst.dims[2]] - inst.goal[:, :inst.dims[2]], axis=1)
+    if np.all(np.abs(final - inst.goal_tol) > DELTA):
+        assert v["goal_reached"] == vo["goal_reached"]
+    frag = oracle_lib.fragile(op, want, DELTA)
+    assert abs(v["reward"] - vo["reward"]) <= 1e-3 * abs(vo["reward"]) + 1e-5 + frag * inst.w_safe / (n * T)
+    if n > 1:
+        assert abs(v["min_pair_dist"] - vo["min_pair_dist"]) <= 2e-4
+
+
+# ----------------------------------------------------------------------------- one step
+
+def _check_step(torch, g, o, inst, it, i, max_oracle_samples=None, seed=0):
+    rng = np.random.default_rng(seed)
+    d_u = inst.dims[1]
+    u_base = scenarios.random_controls(rng, inst, scale=0.5).astype(np.float32)
+    du_in = scenarios.random_deformation(rng, inst, scale=0.3).astype(np.float32)
+    prob = g.Problem(inst)
+    p = gpu_params(g, inst)
+    fit = torch.zeros(inst.N, device="cuda")
+    du_out = torch.zeros_like(dev(torch, du_in))
+    g.d4orm_denoise_step(prob.handle, p, it, i, dev(torch, u_base), dev(torch, du_in), du_out, fit)
+    torch.cuda.synchronize()
+    fit_g = host(fit)
+    out_g = host(du_out)
+    op = oracle_problem(o, inst)
+    pp = oracle_params(o, inst)
+    ub64, du64 = u_base.astype(np.float64), du_in.astype(np.float64)
+    # per-sample fitness
+    if max_oracle_samples and inst.N > max_oracle_samples:
+        js = np.sort(rng.choice(inst.N, size=max_oracle_samples, replace=False))
+    else:
+        js = np.arange(inst.N)
+    f_o, _, frag = o.sample_fitness(op, pp, it, i, ub64, du64, js, delta=DELTA, with_fragile=True)
+    tol = 1e-3 * np.abs(f_o) + 1e-5 + frag * inst.w_safe / (inst.n * inst.T)
+    err = np.abs(fit_g[js] - f_o)
+    assert (err <= tol).all(), (err.max(), int((err > tol).sum()))
+    n_fragile = int((frag > 0).sum())
+    # update from the GPU's fitness vector (stage isolation)
+    out_o, _ = o.denoise_step(op, pp, it, i, ub64, du64, fitness_in=fit_g)
+    scale = max(np.abs(out_o).max(), 1e-30)
+    assert np.abs(out_g - out_o).max() <= (1e-3 + 1e-6) * scale, np.abs(out_g - out_o).max() / scale
+    return dict(n_fragile=n_fragile, checked=len(js), fit_g=fit_g, out_g=out_g, u_base=ub64, du_in=du64)
+
+
+STEP_CASES = [
+    # dyn, integ, n, T, N, it, i
+    (0, 0, 3, 13, 200, 0, 20),     # ragged: 3 robots in 4-lane segments, T % 4 = 1, partial CTA
+    (1, 1, 5, 7, 77, 2, 1),        # 3D, d_u = 3, T * d_u % 4 = 1, last step (sigma small)
+    (2, 1, 1, 9, 33, 1, 7),        # one robot: segment of one lane
+    (3, 1, 7, 21, 130, 0, 13),     # 4-state differential drive
+    (0, 1, 32, 10, 64, 1, 5),      # 32 robots: a whole warp per sample
+    (1, 1, 16, 1, 1, 0, 3),        # N = 1, T = 1
+    (2, 0, 6, 30, 300, 4095, 20),  # largest iteration index
+]
+
+
+@pytest.mark.parametrize("dyn,integ,n,T,N,it,i", STEP_CASES)
+def test_denoise_step_parity(torch, g, oracle_lib, dyn, integ, n, T, N, it, i):
+    inst = small_instance(dyn, n, T, N, integ=integ, seed=7, K=20)
+    r = _check_step(torch, g, oracle_lib, inst, it, i)
+    assert r["n_fragile"] <= max(2, 0.02 * N)
+
+
+def test_denoise_step_own_fitness_when_robust(torch, g, oracle_lib):
+    """Full oracle step (its own fitness) vs the GPU when no sample is fragile."""
+    inst = small_instance(0, 4, 30, 256, seed=3, K=20)
+    r = _check_step(torch, g, oracle_lib, inst, 0, 20)
+    if r["n_fragile"] == 0:
+        out_o, _ = oracle_lib.denoise_step(oracle_problem(oracle_lib, inst), oracle_params(oracle_lib, inst), 0, 20,
+                                           r["u_base"], r["du_in"])
+        scale = np.abs(out_o).max()
+        assert np.abs(r["out_g"] - out_o).max() <= 2e-3 * scale
+
+
+@pytest.mark.parametrize("name,it,i,cap", [("holo2d_n4", 0, 100, None), ("unicycle_n8", 3, 100, None),
+                                           ("unicycle_n8", 4, 1, 512), ("holo3d_n16", 1, 60, 384)])
+def test_denoise_step_parity_full_size(torch, g, oracle_lib, name, it, i, cap):
+    """The measured workloads at full size (same launch configuration as the
+    benchmark); the oracle checks all samples or a random subset."""
+    inst = round_instance(scenarios.WORKLOADS[name]())
+    _check_step(torch, g, oracle_lib, inst, it, i, max_oracle_samples=cap, seed=1)
+
+
+def test_denoise_step_is_deterministic(torch, g):
+    inst = small_instance(1, 9, 40, 1000, seed=5)
+    prob = g.Problem(inst)
+    p = gpu_params(g, inst)
+    rng = np.random.default_rng(0)
+    ub = dev(torch, scenarios.random_controls(rng, inst, 0.5))
+    du = dev(torch, scenarios.random_deformation(rng, inst))
+    outs = []
+    for _ in range(2):
+        o = torch.zeros_like(du)
+        f = torch.zeros(inst.N, device="cuda")
+        g.d4orm_denoise_step(prob.handle, p, 1, 10, ub, du, o, f)
+        outs.append((o.clone(), f.clone()))
+    torch.cuda.synchronize()
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+
+
+def test_denoise_step_argument_errors(torch, g):
+    inst = small_instance(0, 2, 5, 8)
+    prob = g.Problem(inst)
+    p = gpu_params(g, inst)
+    a = torch.zeros((5, 2, 2), device="cuda")
+    b = torch.zeros_like(a)
+    for it, i in ((0, 0), (0, inst.K + 1), (-1, 1), (4096, 1)):
+        with pytest.raises(g.D4ormError) as ei:
+            g.d4orm_denoise_step(prob.handle, p, it, i, a, a, b)
+        assert ei.value.status == 1
+    with pytest.raises(g.D4ormError):
+        g.d4orm_denoise_step(prob.handle, p, 0, 1, a, a, a)   # du_out aliases du_in
+    bad = gpu_params(g, inst)
+    bad.temperature = 0.0
+    with pytest.raises(g.D4ormError):
+        g.d4orm_denoise_step(prob.handle, bad, 0, 1, a, a, b)
+
+
+# ----------------------------------------------------------------------------- solve
+
+def test_solve_matches_eager_steps(torch, g):
+    """One solve iteration (graph replay) equals K eager denoise steps followed
+    by tau.u = clip(0 + dU_0), bit for bit."""
+    inst = small_instance(0, 4, 24, 128, seed=9, K=12)
+    prob = g.Problem(inst)
+    p = gpu_params(g, inst)
+    nctrl = (inst.T, inst.n, 2)
+    u_out = torch.zeros(nctrl, device="cuda")
+    res = g.d4orm_solve(prob.handle, p, g.Budget(max_iters=1), u_out)
+    zero = torch.zeros(nctrl, device="cuda")
+    du = torch.zeros(nctrl, device="cuda")
+    for i in range(inst.K, 0, -1):
+        nxt = torch.zeros_like(du)
+        g.d4orm_denoise_step(prob.handle, p, 0, i, zero, du, nxt)
+        du = nxt
+    lo = torch.tensor(inst.u_lo, device="cuda")
+    hi = torch.tensor(inst.u_hi, device="cuda")
+    want = torch.minimum(torch.maximum(du, lo), hi)
+    torch.cuda.synchronize()
+    assert torch.equal(u_out, want)
+    assert res["iters_run"] == 1
+    v = g.d4orm_rollout(prob.handle, p, u_out)
+    assert v == res["verdict"]
+
+
+def test_solve_verdict_parity_holo2d_n4(torch, g, oracle_lib):
+    """The 4-robot Euler workload solved end to end by both implementations:
+    identical collision-free / goal-reached verdicts, and the oracle's
+    verdict of the GPU's own plan agrees with the GPU's."""
+    inst = round_instance(scenarios.holo2d_circle_n4())
+    prob = g.Problem(inst)
+    p = gpu_params(g, inst)
+    u_out = torch.zeros((inst.T, inst.n, 2), device="cuda")
+    res = g.d4orm_solve(prob.handle, p, g.Budget(max_iters=1), u_out)
+    op, pp = oracle_problem(oracle_lib, inst), oracle_params(oracle_lib, inst)
+    u_o, verdicts, _ = oracle_lib.solve(op, pp, 1)
+    st_g = oracle_lib.rollout(op, host(u_out))
+    v_g = oracle_lib.verdict(op, inst.w_safe, st_g)
+    assert res["verdict"]["collision_free"] == v_g["collision_free"]
+    assert res["verdict"]["goal_reached"] == v_g["goal_reached"]
+    assert res["verdict"]["collision_free"] == verdicts[-1]["collision_free"]
+    assert res["verdict"]["goal_reached"] == verdicts[-1]["goal_reached"] is False  # 6 m in 5 s is infeasible
+
+
+def test_solve_swap_succeeds_like_oracle(torch, g, oracle_lib):
+    start = np.array([[-1.5, 0, 0, 0], [1.5, 0, 0, 0]])
+    inst = scenarios.Instance("swap", 0, 1, 2, 60, 0.1, 0.2, (-1.0, -1.0), (1.0, 1.0), 1.0, start, -start,
+                              N=256, K=100, iters=6, seed=0)
+    inst = round_instance(inst)
+    prob = g.Problem(inst)
+    p = gpu_params(g, inst)
+    u_out = torch.zeros((inst.T, 2, 2), device="cuda")
+    res = g.d4orm_solve(prob.handle, p, g.Budget(max_iters=6, stop_on_success=True), u_out)
+    _, verdicts, first = oracle_lib.solve(oracle_problem(oracle_lib, inst), oracle_params(oracle_lib, inst), 6,
+                                          stop_on_success=True)
+    assert first >= 0 and res["first_success_iter"] >= 0
+    assert res["verdict"]["collision_free"] and res["verdict"]["goal_reached"]
+    assert res["iters_run"] == res["first_success_iter"] + 1
+
+
+def test_solve_budget_paths(torch, g):
+    inst = small_instance(2, 3, 20, 64, seed=4, K=10)
+    prob = g.Problem(inst)
+    p = gpu_params(g, inst)
+    u_out = torch.zeros((inst.T, 3, 2), device="cuda")
+    r = g.d4orm_solve(prob.handle, p, g.Budget(max_iters=3), u_out)
+    assert r["iters_run"] == 3 and r["ms_total"] > 0
+    r2 = g.d4orm_solve(prob.handle, p, g.Budget(max_iters=3, deadline_ms=1e-6), u_out)
+    assert r2["iters_run"] == 1
+    # warm start: first iteration runs steps start_step..1 from du_init
+    du0 = torch.full((inst.T, 3, 2), 0.05, device="cuda")
+    r3 = g.d4orm_solve(prob.handle, p, g.Budget(max_iters=2, start_step=4), u_out, du_init_dev=du0)
+    assert r3["iters_run"] == 2
+    with pytest.raises(g.D4ormError):
+        g.d4orm_solve(prob.handle, p, g.Budget(max_iters=2, start_step=0), u_out, du_init_dev=du0)
+    with pytest.raises(g.D4ormError):
+        g.d4orm_solve(prob.handle, p, g.Budget(max_iters=0), u_out)
