@@ -174,6 +174,36 @@ d4orm_status d4orm_denoise_step_timed(d4orm_problem *problem, const d4orm_params
                                       const float *u_base_dev, const float *du_in_dev, float *du_out_dev,
                                       float *fitness_dev, float *kernel_ms_host, void *stream);
 
+/* Allocation-free denoising step.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc -- a planner inside a
+ * robot's real-time control loop, where cudaMalloc may synchronise the
+ * device and has no latency bound, or a host application that reserves all
+ * device memory in its own pool up front and forbids allocations by
+ * libraries.  It computes exactly what d4orm_denoise_step computes (same
+ * kernels, same launch shapes), but its scratch (weights, fitness when
+ * fitness_dev is NULL, per-chunk partial sums) lives in a fixed 2 MiB array
+ * inside the library's device image instead of the problem's workspace, so
+ * the call allocates nothing: no cudaMalloc, no cudaFree, no allocating
+ * library routine.  (d4orm_problem_create allocates no device memory.)
+ * The caller still passes every input and output buffer.
+ *  - Limits: n_samples <= D4ORM_NOALLOC_MAX_SAMPLES, and the problem's
+ *    scratch must fit in D4ORM_NOALLOC_SCRATCH_FLOATS floats (every problem
+ *    create accepts does on GPUs with up to 152 SMs); beyond either the call
+ *    returns D4ORM_ERR_UNSUPPORTED before launching anything.
+ *  - The first call on each device does a one-time set-up with that device
+ *    current (looks up the array's device address, reads the SM count, sets
+ *    kernel attributes); make that first call before any stream capture.
+ *  - Every call on a device shares the one array, which keeps the last
+ *    call's contents (nothing in it needs to start at zero: each call writes
+ *    all it reads).  Calls whose GPU work overlaps -- on different streams or
+ *    from different host threads -- race on it; serialise them.
+ *  - Arguments and errors as d4orm_denoise_step. */
+#define D4ORM_NOALLOC_SCRATCH_FLOATS (1 << 19)
+#define D4ORM_NOALLOC_MAX_SAMPLES 65536
+d4orm_status d4orm_denoise_step_noalloc(const d4orm_problem *problem, const d4orm_params *params, int iter,
+                                        int step_i, const float *u_base_dev, const float *du_in_dev,
+                                        float *du_out_dev, float *fitness_dev, void *stream);
+
 /* Algorithm 2 with an anytime budget.  tau.u starts at zero.  Each
  * iteration runs steps K..1 from dU_K = 0 (Sec. IV-D), or, in the first
  * iteration when du_init_dev is given, steps start_step..1 from

@@ -26,6 +26,8 @@ MAX_ROBOTS = 32
 MAX_ITERS = 4096
 MAX_TAG = (1 << 20) - 1
 MAX_CTRL = 49152
+NOALLOC_SCRATCH_FLOATS = 1 << 19
+NOALLOC_MAX_SAMPLES = 65536
 
 STATUS = {0: "D4ORM_OK", 1: "D4ORM_ERR_INVALID_ARG", 2: "D4ORM_ERR_UNSUPPORTED", 3: "D4ORM_ERR_OOM",
           4: "D4ORM_ERR_CUDA", 5: "D4ORM_ERR_TIMEOUT", 6: "D4ORM_ERR_CANCELLED"}
@@ -33,7 +35,7 @@ STATUS = {0: "D4ORM_OK", 1: "D4ORM_ERR_INVALID_ARG", 2: "D4ORM_ERR_UNSUPPORTED",
 # Every entry point declared in include/d4orm.h.
 EXPORTS = (
     "d4orm_problem_create", "d4orm_problem_destroy", "d4orm_rollout", "d4orm_denoise_step",
-    "d4orm_denoise_step_timed", "d4orm_solve",
+    "d4orm_denoise_step_timed", "d4orm_denoise_step_noalloc", "d4orm_solve",
     "d4orm_sample_noise", "d4orm_philox4x32_10", "d4orm_status_string", "d4orm_last_error",
 )
 
@@ -101,6 +103,8 @@ def _load() -> ctypes.CDLL:
     lib.d4orm_denoise_step_timed.argtypes = [vp, ctypes.POINTER(_Params), i, i, vp, vp, vp, vp,
                                              ctypes.POINTER(ctypes.c_float), vp]
     lib.d4orm_denoise_step_timed.restype = i
+    lib.d4orm_denoise_step_noalloc.argtypes = [vp, ctypes.POINTER(_Params), i, i, vp, vp, vp, vp, vp]
+    lib.d4orm_denoise_step_noalloc.restype = i
     lib.d4orm_solve.argtypes = [vp, ctypes.POINTER(_Params), ctypes.POINTER(_Budget), vp, vp,
                                 ctypes.POINTER(_Result), vp]
     lib.d4orm_solve.restype = i
@@ -233,6 +237,16 @@ def d4orm_denoise_step_timed(handle, params: Params, iter: int, step_i: int, u_b
     _check(lib.d4orm_denoise_step_timed(handle, ctypes.byref(pc), iter, step_i, _ptr(u_base_dev), _ptr(du_in_dev),
                                         _ptr(du_out_dev), _ptr(fitness_dev), ms, _stream(stream)))
     return list(ms)
+
+
+def d4orm_denoise_step_noalloc(handle, params: Params, iter: int, step_i: int, u_base_dev, du_in_dev, du_out_dev,
+                               fitness_dev=None, stream=None) -> None:
+    """d4orm_denoise_step for callers that cannot allocate device memory: the
+    scratch lives in a fixed array of the library's device image (shared by
+    all calls on a device; overlapping calls race)."""
+    pc = params.c()
+    _check(lib.d4orm_denoise_step_noalloc(handle, ctypes.byref(pc), iter, step_i, _ptr(u_base_dev),
+                                          _ptr(du_in_dev), _ptr(du_out_dev), _ptr(fitness_dev), _stream(stream)))
 
 
 def d4orm_solve(handle, params: Params, budget: Budget, u_out_dev, du_init_dev=None, stream=None) -> dict:

@@ -588,3 +588,36 @@ d4orm_status d4orm_philox4x32_10(const uint32_t* ctr_dev, uint32_t key0, uint32_
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Accessors for other translation units of the library (same validation,
+// schedule and per-step constants as the entry points above).
+// ---------------------------------------------------------------------------
+namespace d4orm {
+
+d4orm_status validate_step_args(const d4orm_problem* P, const d4orm_params* params, int iter, int step_i,
+                                const float* u_base_dev, const float* du_in_dev, const float* du_out_dev)
+{
+    d4orm_status s = check_params(P, params);
+    if (s != D4ORM_OK) return s;
+    if (!u_base_dev || !du_in_dev || !du_out_dev) return fail(D4ORM_ERR_INVALID_ARG, "null device buffer");
+    if (du_in_dev == du_out_dev) return fail(D4ORM_ERR_INVALID_ARG, "du_out_dev must not alias du_in_dev");
+    if (step_i < 1 || step_i > params->n_steps) return fail(D4ORM_ERR_INVALID_ARG, "step_i out of 1..K");
+    if (iter < 0 || iter >= D4ORM_MAX_ITERS) return fail(D4ORM_ERR_INVALID_ARG, "iter out of range");
+    return D4ORM_OK;
+}
+
+DevStep make_step_consts(const d4orm_params* params, int iter, int step_i)
+{
+    std::vector<double> abar;
+    schedule(params, abar);
+    return step_consts(params, abar, iter, step_i);
+}
+
+const DevProblem& dev_problem(const d4orm_problem* P) { return P->dp; }
+
+d4orm_status set_error(d4orm_status s, const char* msg) { return fail(s, "%s", msg); }
+
+d4orm_status set_cuda_error(cudaError_t e, const char* where) { return cuda_fail(e, where); }
+
+}  // namespace d4orm

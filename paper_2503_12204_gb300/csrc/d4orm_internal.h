@@ -50,4 +50,12 @@ cudaError_t launch_sample_noise(const DevProblem& P, const DevStep& S, int j0, i
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t key0, uint32_t key1, int count, uint32_t* out,
                           cudaStream_t st);
 
+// Shared host-side helpers defined in d4orm_capi.cu.
+d4orm_status validate_step_args(const d4orm_problem* P, const d4orm_params* params, int iter, int step_i,
+                                const float* u_base_dev, const float* du_in_dev, const float* du_out_dev);
+DevStep make_step_consts(const d4orm_params* params, int iter, int step_i);
+const DevProblem& dev_problem(const d4orm_problem* P);
+d4orm_status set_error(d4orm_status s, const char* msg);
+d4orm_status set_cuda_error(cudaError_t e, const char* where);
+
 }  // namespace d4orm
