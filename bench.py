@@ -310,6 +310,8 @@ def run_ours(args):
     step_ms = float(kms.sum(axis=1).mean())
     share = (kms.mean(axis=0) / kms.mean(axis=0).sum()).tolist()
     flops = flops_per_sample_rollout(inst) * inst.N
+    k2_kind = g.d4orm_problem_rollout_kernel(prob.handle, inst.N)
+    k2_name = {g.ROLLOUT_REGISTER: "k_rollout_fitness", g.ROLLOUT_PIPELINE: "k_rollout_fitness_pipe"}.get(k2_kind, "?")
     props = torch.cuda.get_device_properties(0)
     csum = clocks.summary()
     peak = fp32_peak_tflops(props.multi_processor_count, 2070.0)
@@ -329,7 +331,7 @@ def run_ours(args):
         "clocks": csum,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "k_rollout_fitness", "peak_basis": "FP32 lanes x 2 x 2070 MHz (152 SMs x 128)",
+                     "kernel": k2_name, "peak_basis": "FP32 lanes x 2 x 2070 MHz (152 SMs x 128)",
                      "flops_per_launch": flops, "launch_ms": k2_ms},
         "kernel_share": {"rollout_fitness": share[0], "softmax_weights": share[1], "weighted_sum": share[2],
                          "finalize": share[3], "eager_step_ms": step_ms},

@@ -142,6 +142,28 @@ d4orm_status d4orm_problem_create(const d4orm_problem_desc *desc, d4orm_problem 
  * the handle issued).  NULL is a no-op. */
 void d4orm_problem_destroy(d4orm_problem *problem);
 
+/* Rollout + fitness kernel used by the denoising steps of a problem.
+ * REGISTER: one warp holds 32/SEG samples (SEG = next power of two >= n),
+ * robots in lanes, state in registers over the whole horizon, pair terms by
+ * shuffles.  PIPELINE: one rollout warp per 32/SEG samples plus helper warps
+ * that generate the noise of the next time chunk and score the previous one
+ * (for batches too small to fill the GPU with the register kernel).  AUTO
+ * picks by batch size.  Both compute the same fitness (summation order
+ * aside). */
+typedef enum {
+    D4ORM_ROLLOUT_AUTO = 0,
+    D4ORM_ROLLOUT_REGISTER = 1,
+    D4ORM_ROLLOUT_PIPELINE = 2
+} d4orm_rollout_kernel;
+
+/* Choose the rollout kernel of a problem (default AUTO).  Host only.
+ * Errors: INVALID_ARG for a null problem or an unknown kind. */
+d4orm_status d4orm_problem_set_rollout_kernel(d4orm_problem *problem, int kernel);
+
+/* The kernel (REGISTER or PIPELINE) the problem's steps use for n_samples
+ * samples on the current device; -1 on error. */
+int d4orm_problem_rollout_kernel(const d4orm_problem *problem, int n_samples);
+
 /* Rollout of one plan (Sec. IV-C; Algorithm 1 final line, Algorithm 2
  * update): controls u_dev[T][n][d_u] are held to the control box and
  * integrated from S.  states_dev (nullable) receives float[T+1][n][d_x].
@@ -169,7 +191,9 @@ d4orm_status d4orm_denoise_step(d4orm_problem *problem, const d4orm_params *para
 /* d4orm_denoise_step with a CUDA event recorded on `stream` between its
  * kernels; synchronises and writes the device time of each kernel, in ms,
  * to kernel_ms_host[4]: {rollout+fitness, softmax weights, weighted noise
- * sum, finalize}.  Results are identical to d4orm_denoise_step. */
+ * sum, finalize}.  A ~200 us sleep kernel runs first so that the events
+ * bracket device time, not host submission.  Results are identical to
+ * d4orm_denoise_step. */
 d4orm_status d4orm_denoise_step_timed(d4orm_problem *problem, const d4orm_params *params, int iter, int step_i,
                                       const float *u_base_dev, const float *du_in_dev, float *du_out_dev,
                                       float *fitness_dev, float *kernel_ms_host, void *stream);

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libd4orm.so")
 
 HOLO2D, HOLO3D, UNICYCLE, DIFFDRIVE4 = 0, 1, 2, 3
 EULER, RK4 = 0, 1
+ROLLOUT_AUTO, ROLLOUT_REGISTER, ROLLOUT_PIPELINE = 0, 1, 2
 DIMS = {HOLO2D: (4, 2, 2), HOLO3D: (6, 3, 3), UNICYCLE: (3, 2, 2), DIFFDRIVE4: (4, 2, 2)}
 MAX_ROBOTS = 32
 MAX_ITERS = 4096
@@ -34,7 +35,8 @@ STATUS = {0: "D4ORM_OK", 1: "D4ORM_ERR_INVALID_ARG", 2: "D4ORM_ERR_UNSUPPORTED",
 
 # Every entry point declared in include/d4orm.h.
 EXPORTS = (
-    "d4orm_problem_create", "d4orm_problem_destroy", "d4orm_rollout", "d4orm_denoise_step",
+    "d4orm_problem_create", "d4orm_problem_destroy", "d4orm_problem_set_rollout_kernel",
+    "d4orm_problem_rollout_kernel", "d4orm_rollout", "d4orm_denoise_step",
     "d4orm_denoise_step_timed", "d4orm_denoise_step_noalloc", "d4orm_solve",
     "d4orm_sample_noise", "d4orm_philox4x32_10", "d4orm_status_string", "d4orm_last_error",
 )
@@ -96,6 +98,10 @@ def _load() -> ctypes.CDLL:
     lib.d4orm_problem_create.restype = i
     lib.d4orm_problem_destroy.argtypes = [vp]
     lib.d4orm_problem_destroy.restype = None
+    lib.d4orm_problem_set_rollout_kernel.argtypes = [vp, i]
+    lib.d4orm_problem_set_rollout_kernel.restype = i
+    lib.d4orm_problem_rollout_kernel.argtypes = [vp, i]
+    lib.d4orm_problem_rollout_kernel.restype = i
     lib.d4orm_rollout.argtypes = [vp, ctypes.POINTER(_Params), vp, vp, ctypes.POINTER(_Verdict), vp]
     lib.d4orm_rollout.restype = i
     lib.d4orm_denoise_step.argtypes = [vp, ctypes.POINTER(_Params), i, i, vp, vp, vp, vp, vp]
@@ -211,6 +217,14 @@ def d4orm_problem_create(n_robots: int, T: int, dyn: int, integ: int, dt: float,
 
 def d4orm_problem_destroy(handle) -> None:
     lib.d4orm_problem_destroy(handle)
+
+
+def d4orm_problem_set_rollout_kernel(handle, kernel: int) -> None:
+    _check(lib.d4orm_problem_set_rollout_kernel(handle, kernel))
+
+
+def d4orm_problem_rollout_kernel(handle, n_samples: int) -> int:
+    return lib.d4orm_problem_rollout_kernel(handle, n_samples)
 
 
 def d4orm_rollout(handle, params: Params | None, u_dev, states_dev=None, want_verdict: bool = True, stream=None):

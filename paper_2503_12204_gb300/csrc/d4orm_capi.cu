@@ -73,10 +73,12 @@ struct d4orm_problem {
     DevProblem dp;
     int device = 0;
     int sm_count = 0;
+    int rollout_kernel = D4ORM_ROLLOUT_AUTO;
     // workspace
     int ws_N = 0;
     float* d_fit = nullptr;      // [N]
-    float* d_w = nullptr;        // [N]
+    float2* d_list = nullptr;    // [N] (weight, sample index) of the samples that carry weight
+    int* d_count = nullptr;      // list length
     float* d_stats = nullptr;    // [4]
     float* d_partial = nullptr;  // [chunks][n*Q][4]
     size_t partial_cap = 0;      // floats
@@ -121,6 +123,7 @@ d4orm_status ensure_workspace(d4orm_problem* P, int N)
             cudaMalloc(&P->d_du[0], nctrl * sizeof(float)) != cudaSuccess ||
             cudaMalloc(&P->d_du[1], nctrl * sizeof(float)) != cudaSuccess ||
             cudaMalloc(&P->d_stats, 4 * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&P->d_count, sizeof(int)) != cudaSuccess ||
             cudaMalloc(&P->d_it, sizeof(int)) != cudaSuccess ||
             cudaMalloc(&P->d_verdicts, (1 + D4ORM_MAX_ITERS) * sizeof(d4orm_verdict)) != cudaSuccess ||
             cudaMallocHost(&P->h_verdicts, (1 + D4ORM_MAX_ITERS) * sizeof(d4orm_verdict)) != cudaSuccess) {
@@ -131,10 +134,11 @@ d4orm_status ensure_workspace(d4orm_problem* P, int N)
     if (N > P->ws_N) {
         free_graphs(P);
         cudaFree(P->d_fit);
-        cudaFree(P->d_w);
-        P->d_fit = P->d_w = nullptr;
+        cudaFree(P->d_list);
+        P->d_fit = nullptr;
+        P->d_list = nullptr;
         if (cudaMalloc(&P->d_fit, (size_t)N * sizeof(float)) != cudaSuccess ||
-            cudaMalloc(&P->d_w, (size_t)N * sizeof(float)) != cudaSuccess) {
+            cudaMalloc(&P->d_list, (size_t)N * sizeof(float2)) != cudaSuccess) {
             cudaGetLastError();
             P->ws_N = 0;
             return fail(D4ORM_ERR_OOM, "workspace allocation for N=%d failed", N);
@@ -190,6 +194,10 @@ DevStep step_consts(const d4orm_params* p, const std::vector<double>& abar, int 
     DevStep S;
     S.key0 = (uint32_t)(p->seed & 0xffffffffu);
     S.key1 = (uint32_t)(p->seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        S.rk0[r] = S.key0 + (uint32_t)r * 0x9E3779B9u;
+        S.rk1[r] = S.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
     S.c2_step = (uint32_t)i << 8;
     S.c3_tag = p->instance_tag << 12;
     S.it = it;
@@ -208,9 +216,9 @@ d4orm_status enqueue_step(d4orm_problem* P, const DevStep& S, const float* u_bas
 {
     const SumSplit sp = plan_weighted_sum(P->dp, S.N, P->sm_count);
     float* fit = fitness ? fitness : P->d_fit;
-    D4_CUDA(launch_rollout_fitness(P->dp, S, u_base, du_in, fit, it_dev, st));
-    D4_CUDA(launch_softmax_weights(fit, S.N, S.inv_lambda, P->d_w, P->d_stats, st));
-    D4_CUDA(launch_weighted_sum(P->dp, S, P->d_w, sp, P->d_partial, it_dev, st));
+    D4_CUDA(launch_rollout_fitness(P->dp, S, u_base, du_in, fit, it_dev, P->sm_count, P->rollout_kernel, st));
+    D4_CUDA(launch_softmax_weights(fit, S.N, S.inv_lambda, P->d_list, P->d_count, P->d_stats, st));
+    D4_CUDA(launch_weighted_sum(P->dp, S, P->d_list, P->d_count, sp, P->d_partial, it_dev, st));
     D4_CUDA(launch_finalize(P->dp, S, P->d_partial, sp, du_in, du_out, st));
     return D4ORM_OK;
 }
@@ -392,7 +400,8 @@ void d4orm_problem_destroy(d4orm_problem* P)
         cudaDeviceSynchronize();
         free_graphs(P);
         cudaFree(P->d_fit);
-        cudaFree(P->d_w);
+        cudaFree(P->d_list);
+        cudaFree(P->d_count);
         cudaFree(P->d_stats);
         cudaFree(P->d_partial);
         cudaFree(P->d_tau_u);
@@ -404,6 +413,33 @@ void d4orm_problem_destroy(d4orm_problem* P)
         cudaSetDevice(cur);
     }
     delete P;
+}
+
+d4orm_status d4orm_problem_set_rollout_kernel(d4orm_problem* P, int kernel)
+{
+    if (!P) return fail(D4ORM_ERR_INVALID_ARG, "null problem");
+    if (kernel != D4ORM_ROLLOUT_AUTO && kernel != D4ORM_ROLLOUT_REGISTER && kernel != D4ORM_ROLLOUT_PIPELINE)
+        return fail(D4ORM_ERR_INVALID_ARG, "unknown rollout kernel %d", kernel);
+    if (kernel != P->rollout_kernel) {
+        free_graphs(P);
+        P->rollout_kernel = kernel;
+    }
+    return D4ORM_OK;
+}
+
+int d4orm_problem_rollout_kernel(const d4orm_problem* P, int n_samples)
+{
+    if (!P || n_samples < 1) return -1;
+    int sms = P->sm_count;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return -1;
+        }
+    }
+    return resolve_rollout_kernel(P->dp, n_samples, sms, P->rollout_kernel);
 }
 
 d4orm_status d4orm_rollout(d4orm_problem* P, const d4orm_params* params, const float* u_dev, float* states_dev,
@@ -544,12 +580,16 @@ d4orm_status d4orm_denoise_step_timed(d4orm_problem* P, const d4orm_params* para
     float* fit = fitness_dev ? fitness_dev : P->d_fit;
     cudaEvent_t ev[5];
     for (int k = 0; k < 5; ++k) D4_CUDA(cudaEventCreate(&ev[k]));
-    cudaError_t e = cudaEventRecord(ev[0], st);
-    if (e == cudaSuccess) e = launch_rollout_fitness(P->dp, S, u_base_dev, du_in_dev, fit, nullptr, st);
+    // a short sleep first, so that every kernel below is already submitted
+    // when the first event fires: the events then bracket device time only
+    cudaError_t e = launch_hold(200, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+    if (e == cudaSuccess) e = launch_rollout_fitness(P->dp, S, u_base_dev, du_in_dev, fit, nullptr, P->sm_count,
+                                                             P->rollout_kernel, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
-    if (e == cudaSuccess) e = launch_softmax_weights(fit, S.N, S.inv_lambda, P->d_w, P->d_stats, st);
+    if (e == cudaSuccess) e = launch_softmax_weights(fit, S.N, S.inv_lambda, P->d_list, P->d_count, P->d_stats, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
-    if (e == cudaSuccess) e = launch_weighted_sum(P->dp, S, P->d_w, sp, P->d_partial, nullptr, st);
+    if (e == cudaSuccess) e = launch_weighted_sum(P->dp, S, P->d_list, P->d_count, sp, P->d_partial, nullptr, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3], st);
     if (e == cudaSuccess) e = launch_finalize(P->dp, S, P->d_partial, sp, du_in_dev, du_out_dev, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[4], st);
@@ -615,6 +655,8 @@ DevStep make_step_consts(const d4orm_params* params, int iter, int step_i)
 }
 
 const DevProblem& dev_problem(const d4orm_problem* P) { return P->dp; }
+
+int rollout_kernel_choice(const d4orm_problem* P) { return P->rollout_kernel; }
 
 d4orm_status set_error(d4orm_status s, const char* msg) { return fail(s, "%s", msg); }
 

@@ -40,6 +40,7 @@ struct DevProblem {
 // Per-step constants of step i in iteration it.
 struct DevStep {
     uint32_t key0, key1;      // Philox key (seed lo, hi)
+    uint32_t rk0[10], rk1[10];// Philox round keys: key + r * Weyl constant
     uint32_t c2_step;         // step_i << 8 (robot index fills the low byte)
     uint32_t c3_tag;          // tag << 12   (iteration fills the low 12 bits)
     int it;                   // iteration (used when no device counter given)
@@ -58,18 +59,31 @@ struct DevStep {
 // ---------------------------------------------------------------------------
 struct U4 { uint32_t x, y, z, w; };
 
+__device__ __forceinline__ U4 philox_round(U4 c, uint32_t k0, uint32_t k1)
+{
+    // one 32x32 -> 64 wide multiply per product: high and low words together
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+    return U4{(uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0};
+}
+
 __device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z;
-        c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+        c = philox_round(c, k0, k1);
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
+    return c;
+}
+
+// Same function with the ten round keys precomputed on the host (uniform
+// kernel parameters: the key schedule costs no instructions per call).
+__device__ __forceinline__ U4 philox4x32_10(U4 c, const DevStep& S)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) c = philox_round(c, S.rk0[r], S.rk1[r]);
     return c;
 }
 
@@ -92,7 +106,7 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, fl
 __device__ __forceinline__ void noise_quad(const DevStep& S, uint32_t c3, uint32_t q, uint32_t j, uint32_t k,
                                            float z[4])
 {
-    const U4 w = philox4x32_10(U4{q, j, (k & 0xffu) | S.c2_step, c3}, S.key0, S.key1);
+    const U4 w = philox4x32_10(U4{q, j, (k & 0xffu) | S.c2_step, c3}, S);
     box_muller(w.x, w.y, z[0], z[1]);
     box_muller(w.z, w.w, z[2], z[3]);
 }
@@ -104,6 +118,27 @@ __device__ __forceinline__ uint32_t iter_word(const DevStep& S, const int* it_de
 }
 
 __device__ __forceinline__ float clampf(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
+
+// Square root on the special-function unit (relative error ~2^-23): used
+// for the Eq. (4) distance, which enters a sum checked to 1e-3.
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// sin/cos of an arbitrary heading: Cody-Waite reduction by 2*pi (Cody and
+// Waite, 1980; 2*pi split into 6.28125 + a binary32 tail, the first part
+// with few enough bits that k * 6.28125 is exact), then the hardware
+// sin/cos on [-pi, pi] (absolute error below 4e-7 there).
+__device__ __forceinline__ void sincos_heading(float th, float* s, float* c)
+{
+    const float k = rintf(th * 0.15915494309189535f);
+    float r = fmaf(-k, 6.28125f, th);
+    r = fmaf(-k, 1.9353071795864769e-3f, r);
+    __sincosf(r, s, c);
+}
 
 // ---------------------------------------------------------------------------
 // One integration step (Sec. III Eq. (1) feasibility; dynamics of Sec. V).
@@ -137,10 +172,10 @@ __device__ __forceinline__ void integrate(float* x, const float* u, const DevPro
     } else if constexpr (DYN == UNICYCLE) {
         const float v = u[0], w = u[1];
         float s0, c0;
-        sincosf(x[2], &s0, &c0);
+        sincos_heading(x[2], &s0, &c0);
         if (P.integ == 1) {
             float sh, ch;
-            sincosf(0.5f * w * P.dt, &sh, &ch);
+            sincos_heading(0.5f * w * P.dt, &sh, &ch);
             const float c1 = c0 * ch - s0 * sh, s1 = s0 * ch + c0 * sh;
             const float c2 = c1 * ch - s1 * sh, s2 = s1 * ch + c1 * sh;
             const float k = P.dt6 * v;
@@ -154,10 +189,10 @@ __device__ __forceinline__ void integrate(float* x, const float* u, const DevPro
     } else {  // DIFFDRIVE4: x = [px, py, theta, v], u = [omega, a]
         const float w = u[0], a = u[1], v = x[3];
         float s0, c0;
-        sincosf(x[2], &s0, &c0);
+        sincos_heading(x[2], &s0, &c0);
         if (P.integ == 1) {
             float sh, ch;
-            sincosf(0.5f * w * P.dt, &sh, &ch);
+            sincos_heading(0.5f * w * P.dt, &sh, &ch);
             const float c1 = c0 * ch - s0 * sh, s1 = s0 * ch + c0 * sh;
             const float c2 = c1 * ch - s1 * sh, s2 = s1 * ch + c1 * sh;
             const float vm = fmaf(0.5f * P.dt, a, v), ve = fmaf(P.dt, a, v);

@@ -19,19 +19,32 @@ SumSplit plan_weighted_sum(const DevProblem& P, int N, int sm_count);
 
 // Kernel attributes K2 needs for problem P (call outside stream capture).
 cudaError_t prepare_rollout_fitness(const DevProblem& P);
+cudaError_t prepare_rollout_fitness_pipe(const DevProblem& P);
+
+// Which rollout kernel serves (P, N): D4ORM_ROLLOUT_REGISTER or
+// D4ORM_ROLLOUT_PIPELINE (requested AUTO picks by how full the register
+// kernel would keep the GPU).
+int resolve_rollout_kernel(const DevProblem& P, int N, int sm_count, int requested);
 
 // K2: fused sample rollout + fitness (Eq. (12) samples, Eq. (1) rollout,
-// Eq. (3)-(5) reward).  fitness[N].
+// Eq. (3)-(5) reward).  fitness[N].  `kernel` is a d4orm_rollout_kernel.
 cudaError_t launch_rollout_fitness(const DevProblem& P, const DevStep& S, const float* u_base,
-                                   const float* du_in, float* fitness, const int* it_dev, cudaStream_t st);
-
-// K3a: batch z-score + softmax (Sec. IV-C, Eq. (6)).  w[N] (normalised).
-cudaError_t launch_softmax_weights(const float* fitness, int N, float inv_lambda, float* w, float* stats,
+                                   const float* du_in, float* fitness, const int* it_dev, int sm_count, int kernel,
                                    cudaStream_t st);
+// K2p: the warp-specialised variant (same results up to summation order).
+cudaError_t launch_rollout_fitness_pipe(const DevProblem& P, const DevStep& S, const float* u_base,
+                                        const float* du_in, float* fitness, const int* it_dev, cudaStream_t st);
+size_t rollout_fitness_pipe_smem(const DevProblem& P);
 
-// K3b: partial[c][n*Q][4] = sum over samples j of chunk c of w_j eps_j.
-cudaError_t launch_weighted_sum(const DevProblem& P, const DevStep& S, const float* w, SumSplit split,
-                                float* partial, const int* it_dev, cudaStream_t st);
+// K3a: batch z-score + softmax (Sec. IV-C, Eq. (6)); writes the ordered
+// list of (normalised weight, sample index) of the samples that carry
+// weight (list[N] capacity) and its length to *count.
+cudaError_t launch_softmax_weights(const float* fitness, int N, float inv_lambda, float2* list, int* count,
+                                   float* stats, cudaStream_t st);
+
+// K3b: partial[c][n*Q][4] = sum of w_j eps_j over the list entries dealt to chunk c.
+cudaError_t launch_weighted_sum(const DevProblem& P, const DevStep& S, const float2* list, const int* count,
+                                SumSplit split, float* partial, const int* it_dev, cudaStream_t st);
 
 // K3c: du_out = g (c du_in + sigma sum_c partial[c])  (Eq. (13)).
 cudaError_t launch_finalize(const DevProblem& P, const DevStep& S, const float* partial, SumSplit split,
@@ -44,7 +57,8 @@ cudaError_t launch_apply_rollout_verdict(const DevProblem& P, float w_safe, cons
                                          float* u_out, float* states, d4orm_verdict* verdict, int* it_inc,
                                          cudaStream_t st);
 
-// Diagnostics: regenerated noise and raw Philox.
+// Diagnostics: a bounded sleep, regenerated noise and raw Philox.
+cudaError_t launch_hold(int microseconds, cudaStream_t st);
 cudaError_t launch_sample_noise(const DevProblem& P, const DevStep& S, int j0, int count, float* eps,
                                 cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t key0, uint32_t key1, int count, uint32_t* out,
@@ -55,6 +69,7 @@ d4orm_status validate_step_args(const d4orm_problem* P, const d4orm_params* para
                                 const float* u_base_dev, const float* du_in_dev, const float* du_out_dev);
 DevStep make_step_consts(const d4orm_params* params, int iter, int step_i);
 const DevProblem& dev_problem(const d4orm_problem* P);
+int rollout_kernel_choice(const d4orm_problem* P);
 d4orm_status set_error(d4orm_status s, const char* msg);
 d4orm_status set_cuda_error(cudaError_t e, const char* where);
 

@@ -4,15 +4,15 @@
 // control loop, where cudaMalloc may synchronise the device and has no
 // latency bound, and host applications that reserve all device memory up
 // front in their own pool and forbid allocations by plug-in libraries.
-// d4orm_denoise_step gets its scratch (fitness, weights, per-chunk partial
-// sums) from the problem's workspace, which it allocates on first use; this
+// d4orm_denoise_step gets its scratch (fitness, the compacted weight list,
+// per-chunk partial sums) from the problem's workspace, which it allocates on first use; this
 // variant takes the same scratch from a fixed array that is part of the
 // library's device image, so it never allocates.  The problem handle itself
 // holds no device memory (d4orm_problem_create allocates none).
 //
 // The array is shared by every call on a device and keeps the last call's
 // contents.  Nothing in it needs to start at zero: each step writes every
-// fitness, weight and partial-sum entry it later reads.  Calls whose work
+// fitness, list, count and partial-sum entry it later reads.  Calls whose work
 // overlaps on the GPU (other streams, or other host threads) race on it.
 #include <mutex>
 
@@ -93,21 +93,23 @@ extern "C" d4orm_status d4orm_denoise_step_noalloc(const d4orm_problem* problem,
 
     const DevProblem& P = dev_problem(problem);
     const SumSplit split = plan_weighted_sum(P, N, ds->sm_count);
-    const size_t n_w = pad64((size_t)N), n_fit = pad64((size_t)N), n_stats = 64;
+    const size_t n_w = 2 * pad64((size_t)N), n_fit = pad64((size_t)N), n_stats = 64;
     const size_t n_partial = (size_t)split.chunks * P.n * P.Q * 4;
     if (n_w + n_fit + n_stats + n_partial > kScratchFloats)
         return set_error(D4ORM_ERR_UNSUPPORTED, "d4orm_denoise_step_noalloc: problem needs more scratch than "
                                                 "D4ORM_NOALLOC_SCRATCH_FLOATS");
-    float* w = ds->scratch;
-    float* fit = fitness_dev ? fitness_dev : w + n_w;
-    float* stats = w + n_w + n_fit;
+    float2* list = reinterpret_cast<float2*>(ds->scratch);
+    float* fit = fitness_dev ? fitness_dev : ds->scratch + n_w;
+    float* stats = ds->scratch + n_w + n_fit;
+    int* count = reinterpret_cast<int*>(stats + 8);
     float* partial = stats + n_stats;
 
     const DevStep S = make_step_consts(params, iter, step_i);
     cudaStream_t st = (cudaStream_t)stream;
-    if ((e = launch_rollout_fitness(P, S, u_base_dev, du_in_dev, fit, nullptr, st)) != cudaSuccess ||
-        (e = launch_softmax_weights(fit, N, S.inv_lambda, w, stats, st)) != cudaSuccess ||
-        (e = launch_weighted_sum(P, S, w, split, partial, nullptr, st)) != cudaSuccess ||
+    if ((e = launch_rollout_fitness(P, S, u_base_dev, du_in_dev, fit, nullptr, ds->sm_count,
+                                     rollout_kernel_choice(problem), st)) != cudaSuccess ||
+        (e = launch_softmax_weights(fit, N, S.inv_lambda, list, count, stats, st)) != cudaSuccess ||
+        (e = launch_weighted_sum(P, S, list, count, split, partial, nullptr, st)) != cudaSuccess ||
         (e = launch_finalize(P, S, partial, split, du_in_dev, du_out_dev, st)) != cudaSuccess)
         return set_cuda_error(e, "d4orm_denoise_step_noalloc launch");
     return D4ORM_OK;

@@ -12,8 +12,9 @@
 // Mapping: robots in lanes.  A warp holds 32/SEG samples, one per aligned
 // segment of SEG lanes (SEG = next power of two >= n); the robot state lives
 // in registers for the whole horizon.  Pairwise distances of Eq. (5) are
-// read from the partner lanes with butterfly shuffles inside the segment,
-// and the per-sample fitness is reduced with segment shuffles: nothing but
+// read from the partner lanes with shuffles inside the segment, each
+// unordered pair once (a ballot returns the flag to the partner), and the
+// per-sample fitness is reduced with segment shuffles: nothing but
 // the final float per sample leaves the SM.  The mean controls M are staged
 // once per CTA in shared memory.  The noise eps is regenerated from Philox in
 // registers, four time steps at a time (d_u Philox calls), never stored.
@@ -41,6 +42,7 @@ k_rollout_fitness(const DevProblem P, const DevStep S, const float* __restrict__
 
     const int lane = threadIdx.x & 31;
     const int k = lane & (SEG - 1);
+    const int seg_base = lane & ~(SEG - 1);
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int j = warp * SPW + lane / SEG;
     const bool robot = k < P.n;
@@ -57,6 +59,10 @@ k_rollout_fitness(const DevProblem P, const DevStep S, const float* __restrict__
     const int rowM = P.n * DU;
     const float* Mk = sM + kr * DU;
     float acc = 0.0f;
+    // pair (k, k+s mod SEG) exists when both robots are real
+    bool pair_ok[SEG / 2 > 0 ? SEG / 2 : 1];
+#pragma unroll
+    for (int s = 1; s <= SEG / 2; ++s) pair_ok[s - 1] = robot && (((k + s) & (SEG - 1)) < P.n);
 
     for (int t0 = 0; t0 < P.T; t0 += 4) {
         float eps[4 * DU];
@@ -79,19 +85,28 @@ k_rollout_fitness(const DevProblem P, const DevStep S, const float* __restrict__
                     const float e = x[d] - g[d];
                     dg2 = fmaf(e, e, dg2);
                 }
-                // Eq. (5): any partner inside 2R+eps (squared distances)
+                // Eq. (5): any partner inside 2R+eps.  Each unordered pair
+                // is evaluated once: lane k tests partner k+s (mod SEG) for
+                // s = 1..SEG/2, and a ballot hands the flag to the partner
+                // (for s = SEG/2 both lanes of the pair test it).
                 bool hit = false;
 #pragma unroll
-                for (int s = 1; s < SEG; ++s) {
+                for (int s = 1; s <= SEG / 2; ++s) {
+                    const int src = seg_base + ((k + s) & (SEG - 1));
                     float d2 = 0.0f;
 #pragma unroll
                     for (int d = 0; d < DP; ++d) {
-                        const float e = x[d] - __shfl_xor_sync(kFull, x[d], s);
+                        const float e = x[d] - __shfl_sync(kFull, x[d], src);
                         d2 = fmaf(e, e, d2);
                     }
-                    hit |= ((k ^ s) < P.n) & (d2 <= P.thr2);
+                    const bool h = pair_ok[s - 1] & (d2 <= P.thr2);
+                    hit |= h;
+                    if (2 * s != SEG) {
+                        const unsigned m = __ballot_sync(kFull, h);
+                        hit |= (m >> (seg_base + ((k - s) & (SEG - 1)))) & 1u;
+                    }
                 }
-                if (robot) acc += (1.0f - sqrtf(dg2) * inv_d0) - (hit ? w_safe : 0.0f);
+                if (robot) acc += (1.0f - sqrt_approx(dg2) * inv_d0) - (hit ? w_safe : 0.0f);
             }
         }
     }
@@ -121,6 +136,8 @@ static cudaError_t prepare_dyn(int n)
 
 cudaError_t prepare_rollout_fitness(const DevProblem& P)
 {
+    const cudaError_t e = prepare_rollout_fitness_pipe(P);
+    if (e != cudaSuccess) return e;
     switch (P.dyn) {
     case HOLO2D: return prepare_dyn<HOLO2D>(P.n);
     case HOLO3D: return prepare_dyn<HOLO3D>(P.n);
@@ -130,37 +147,72 @@ cudaError_t prepare_rollout_fitness(const DevProblem& P)
     }
 }
 
+// Warps per CTA: every sample is the same amount of work, so the launch
+// that minimises the most-loaded SM (all CTAs resident in one wave) wins;
+// ties go to wider CTAs (fewer shared-memory loads of the mean controls).
+static int pick_warps_per_cta(int total_warps, int sm_count)
+{
+    int best_w = 1;
+    long long best_cost = -1;
+    for (int w = 1; w <= kK2Threads / 32; ++w) {
+        const long long ctas = (total_warps + w - 1) / w;
+        const long long per_sm = (ctas + sm_count - 1) / sm_count;
+        const long long cost = per_sm * w;
+        if (best_cost < 0 || cost <= best_cost) {
+            best_cost = cost;
+            best_w = w;
+        }
+    }
+    return best_w;
+}
+
 template <int DYN, int SEG>
 static cudaError_t launch_k2(const DevProblem& P, const DevStep& S, const float* u_base, const float* du_in,
-                             float* fitness, const int* it_dev, cudaStream_t st)
+                             float* fitness, const int* it_dev, int sm_count, cudaStream_t st)
 {
-    constexpr int spb = (kK2Threads / 32) * (32 / SEG);
+    constexpr int spw = 32 / SEG;
+    const int total_warps = (S.N + spw - 1) / spw;
+    const int w = pick_warps_per_cta(total_warps, sm_count);
     const size_t smem = (size_t)P.T * P.n * DynDims<DYN>::DU * sizeof(float);
-    const int grid = (S.N + spb - 1) / spb;
-    k_rollout_fitness<DYN, SEG><<<grid, kK2Threads, smem, st>>>(P, S, u_base, du_in, fitness, it_dev);
+    const int grid = (total_warps + w - 1) / w;
+    k_rollout_fitness<DYN, SEG><<<grid, 32 * w, smem, st>>>(P, S, u_base, du_in, fitness, it_dev);
     return cudaGetLastError();
 }
 
 template <int DYN>
 static cudaError_t dispatch_seg(const DevProblem& P, const DevStep& S, const float* u_base, const float* du_in,
-                                float* fitness, const int* it_dev, cudaStream_t st)
+                                float* fitness, const int* it_dev, int sms, cudaStream_t st)
 {
-    if (P.n <= 1) return launch_k2<DYN, 1>(P, S, u_base, du_in, fitness, it_dev, st);
-    if (P.n <= 2) return launch_k2<DYN, 2>(P, S, u_base, du_in, fitness, it_dev, st);
-    if (P.n <= 4) return launch_k2<DYN, 4>(P, S, u_base, du_in, fitness, it_dev, st);
-    if (P.n <= 8) return launch_k2<DYN, 8>(P, S, u_base, du_in, fitness, it_dev, st);
-    if (P.n <= 16) return launch_k2<DYN, 16>(P, S, u_base, du_in, fitness, it_dev, st);
-    return launch_k2<DYN, 32>(P, S, u_base, du_in, fitness, it_dev, st);
+    if (P.n <= 1) return launch_k2<DYN, 1>(P, S, u_base, du_in, fitness, it_dev, sms, st);
+    if (P.n <= 2) return launch_k2<DYN, 2>(P, S, u_base, du_in, fitness, it_dev, sms, st);
+    if (P.n <= 4) return launch_k2<DYN, 4>(P, S, u_base, du_in, fitness, it_dev, sms, st);
+    if (P.n <= 8) return launch_k2<DYN, 8>(P, S, u_base, du_in, fitness, it_dev, sms, st);
+    if (P.n <= 16) return launch_k2<DYN, 16>(P, S, u_base, du_in, fitness, it_dev, sms, st);
+    return launch_k2<DYN, 32>(P, S, u_base, du_in, fitness, it_dev, sms, st);
+}
+
+int resolve_rollout_kernel(const DevProblem& P, int N, int sm_count, int requested)
+{
+    const bool pipe_fits = rollout_fitness_pipe_smem(P) <= 200 * 1024;
+    if (requested == D4ORM_ROLLOUT_PIPELINE && pipe_fits) return D4ORM_ROLLOUT_PIPELINE;
+    if (requested == D4ORM_ROLLOUT_REGISTER || !pipe_fits) return D4ORM_ROLLOUT_REGISTER;
+    // automatic: the register kernel needs about eight warps per SM to hide
+    // its per-step latency; smaller batches expose parallelism along time
+    const int seg = P.n <= 1 ? 1 : P.n <= 2 ? 2 : P.n <= 4 ? 4 : P.n <= 8 ? 8 : P.n <= 16 ? 16 : 32;
+    const long long warps = ((long long)N * seg + 31) / 32;
+    return warps < 8LL * sm_count ? D4ORM_ROLLOUT_PIPELINE : D4ORM_ROLLOUT_REGISTER;
 }
 
 cudaError_t launch_rollout_fitness(const DevProblem& P, const DevStep& S, const float* u_base, const float* du_in,
-                                   float* fitness, const int* it_dev, cudaStream_t st)
+                                   float* fitness, const int* it_dev, int sm_count, int kernel, cudaStream_t st)
 {
+    if (resolve_rollout_kernel(P, S.N, sm_count, kernel) == D4ORM_ROLLOUT_PIPELINE)
+        return launch_rollout_fitness_pipe(P, S, u_base, du_in, fitness, it_dev, st);
     switch (P.dyn) {
-    case HOLO2D: return dispatch_seg<HOLO2D>(P, S, u_base, du_in, fitness, it_dev, st);
-    case HOLO3D: return dispatch_seg<HOLO3D>(P, S, u_base, du_in, fitness, it_dev, st);
-    case UNICYCLE: return dispatch_seg<UNICYCLE>(P, S, u_base, du_in, fitness, it_dev, st);
-    case DIFFDRIVE4: return dispatch_seg<DIFFDRIVE4>(P, S, u_base, du_in, fitness, it_dev, st);
+    case HOLO2D: return dispatch_seg<HOLO2D>(P, S, u_base, du_in, fitness, it_dev, sm_count, st);
+    case HOLO3D: return dispatch_seg<HOLO3D>(P, S, u_base, du_in, fitness, it_dev, sm_count, st);
+    case UNICYCLE: return dispatch_seg<UNICYCLE>(P, S, u_base, du_in, fitness, it_dev, sm_count, st);
+    case DIFFDRIVE4: return dispatch_seg<DIFFDRIVE4>(P, S, u_base, du_in, fitness, it_dev, sm_count, st);
     default: return cudaErrorInvalidValue;
     }
 }

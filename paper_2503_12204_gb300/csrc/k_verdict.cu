@@ -169,6 +169,19 @@ __global__ void k_philox(const uint4* __restrict__ ctr, uint32_t key0, uint32_t 
     out[i] = make_uint4(r.x, r.y, r.z, r.w);
 }
 
+// A fixed-length sleep (bounded: iterations x ~1 us), used to keep the
+// stream busy while the host submits the kernels of a timed step.
+__global__ void k_hold(int iterations)
+{
+    for (int i = 0; i < iterations; ++i) __nanosleep(1000);
+}
+
+cudaError_t launch_hold(int microseconds, cudaStream_t st)
+{
+    k_hold<<<1, 32, 0, st>>>(microseconds);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sample_noise(const DevProblem& P, const DevStep& S, int j0, int count, float* eps,
                                 cudaStream_t st)
 {

@@ -116,12 +116,15 @@ def test_rollout_states_and_verdict(torch, g, oracle_lib, dyn, integ, n, T):
 
 # ----------------------------------------------------------------------------- one step
 
-def _check_step(torch, g, o, inst, it, i, max_oracle_samples=None, seed=0):
+def _check_step(torch, g, o, inst, it, i, max_oracle_samples=None, seed=0, kernel=0):
     rng = np.random.default_rng(seed)
     d_u = inst.dims[1]
     u_base = scenarios.random_controls(rng, inst, scale=0.5).astype(np.float32)
     du_in = scenarios.random_deformation(rng, inst, scale=0.3).astype(np.float32)
     prob = g.Problem(inst)
+    g.d4orm_problem_set_rollout_kernel(prob.handle, kernel)
+    if kernel:
+        assert g.d4orm_problem_rollout_kernel(prob.handle, inst.N) == kernel
     p = gpu_params(g, inst)
     fit = torch.zeros(inst.N, device="cuda")
     du_out = torch.zeros_like(dev(torch, du_in))
@@ -158,14 +161,37 @@ STEP_CASES = [
     (0, 1, 32, 10, 64, 1, 5),      # 32 robots: a whole warp per sample
     (1, 1, 16, 1, 1, 0, 3),        # N = 1, T = 1
     (2, 0, 6, 30, 300, 4095, 20),  # largest iteration index
+    (0, 1, 2, 8, 9000, 0, 10),     # N > 8192: softmax re-reads fitness instead of holding it in registers
 ]
 
 
+@pytest.mark.parametrize("kernel", [1, 2], ids=["register", "pipeline"])
 @pytest.mark.parametrize("dyn,integ,n,T,N,it,i", STEP_CASES)
-def test_denoise_step_parity(torch, g, oracle_lib, dyn, integ, n, T, N, it, i):
+def test_denoise_step_parity(torch, g, oracle_lib, dyn, integ, n, T, N, it, i, kernel):
     inst = small_instance(dyn, n, T, N, integ=integ, seed=7, K=20)
-    r = _check_step(torch, g, oracle_lib, inst, it, i)
+    r = _check_step(torch, g, oracle_lib, inst, it, i, kernel=kernel)
     assert r["n_fragile"] <= max(2, 0.02 * N)
+
+
+@pytest.mark.parametrize("dyn,n,T,N", [(0, 4, 50, 256), (2, 8, 100, 700), (1, 16, 37, 300), (3, 32, 9, 40)])
+def test_rollout_kernels_agree(torch, g, dyn, n, T, N):
+    """The register and pipeline kernels evaluate the same samples with the
+    same arithmetic; only the order of the fitness summation differs."""
+    inst = small_instance(dyn, n, T, N, seed=13, K=20)
+    rng = np.random.default_rng(2)
+    ub = dev(torch, scenarios.random_controls(rng, inst, 0.5))
+    du = dev(torch, scenarios.random_deformation(rng, inst))
+    prob = g.Problem(inst)
+    p = gpu_params(g, inst)
+    fits = []
+    for kernel in (1, 2):
+        g.d4orm_problem_set_rollout_kernel(prob.handle, kernel)
+        f = torch.zeros(N, device="cuda")
+        o = torch.zeros_like(du)
+        g.d4orm_denoise_step(prob.handle, p, 2, 9, ub, du, o, f)
+        fits.append(host(f))
+    torch.cuda.synchronize()
+    assert np.abs(fits[0] - fits[1]).max() <= 2e-6 * max(1.0, np.abs(fits[0]).max())
 
 
 def test_denoise_step_own_fitness_when_robust(torch, g, oracle_lib):
@@ -188,9 +214,11 @@ def test_denoise_step_parity_full_size(torch, g, oracle_lib, name, it, i, cap):
     _check_step(torch, g, oracle_lib, inst, it, i, max_oracle_samples=cap, seed=1)
 
 
-def test_denoise_step_is_deterministic(torch, g):
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_denoise_step_is_deterministic(torch, g, kernel):
     inst = small_instance(1, 9, 40, 1000, seed=5)
     prob = g.Problem(inst)
+    g.d4orm_problem_set_rollout_kernel(prob.handle, kernel)
     p = gpu_params(g, inst)
     rng = np.random.default_rng(0)
     ub = dev(torch, scenarios.random_controls(rng, inst, 0.5))
