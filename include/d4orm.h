@@ -238,6 +238,54 @@ d4orm_status d4orm_denoise_step_noalloc(const d4orm_problem *problem, const d4or
 d4orm_status d4orm_solve(d4orm_problem *problem, const d4orm_params *params, const d4orm_budget *budget,
                          const float *du_init_dev, float *u_out_dev, d4orm_result *out_host, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched persistent solve.  Many independent problems -- any mix of robot
+ * counts, horizons and dynamics -- solved by Algorithm 2 in ONE persistent
+ * kernel launch replayed from a CUDA graph.  Each CTA takes problems from
+ * an atomic work queue (longest first) and runs every step and iteration of
+ * one problem with block-level synchronisation only; CTAs never wait on
+ * each other.  Problem b draws its noise with instance tag
+ * params->instance_tag + b, so it reproduces d4orm_solve of that problem
+ * with that tag (up to the order of floating-point reductions).
+ * ------------------------------------------------------------------------- */
+typedef struct d4orm_batch d4orm_batch;
+
+#define D4ORM_BATCH_MAX_SAMPLES 8192
+
+/* Build a batch over problems[0..count-1] (handles must outlive the batch)
+ * with one set of denoising parameters.  Uploads descriptors and allocates
+ * per-problem workspace.  autotune != 0 times the persistent kernel at 128,
+ * 256 and 512 threads per CTA on a 2-step pilot over the whole batch and
+ * keeps the fastest (see d4orm_batch_info); otherwise 256.
+ * Errors: INVALID_ARG (null arguments, bad params, tags beyond
+ * D4ORM_MAX_TAG), UNSUPPORTED (n_samples > D4ORM_BATCH_MAX_SAMPLES, or
+ * shared memory for the largest problem above 200 KB), OOM, CUDA. */
+d4orm_status d4orm_batch_create(d4orm_problem *const *problems, int count, const d4orm_params *params,
+                                int autotune, d4orm_batch **out);
+
+/* Solve every problem of the batch.  u_out_dev: host array [count] of
+ * device pointers, each [T_b][n_b][d_u_b] (final tau.u).  du_init_dev:
+ * nullable host array [count] of device pointers: warm-start deformations
+ * entering the first iteration at budget->start_step.  out_host (nullable):
+ * [count] results; ms_to_success / ms_total are device-clock times of each
+ * problem's own solve (from when its CTA picked it up).  budget->deadline_ms
+ * must be <= 0 (UNSUPPORTED otherwise).  Synchronises the device before
+ * and `stream` after the launch. */
+d4orm_status d4orm_batch_solve(d4orm_batch *batch, const d4orm_budget *budget, const float *const *du_init_dev,
+                               float *const *u_out_dev, d4orm_result *out_host, void *stream);
+
+/* Launch shape the batch uses and the autotuner's pilot times (ms, -1 when
+ * a width was not tried) for 128 / 256 / 512 threads. */
+d4orm_status d4orm_batch_info(const d4orm_batch *batch, int *threads_per_cta, int *ctas, float *tuned_ms);
+
+/* Free a batch (synchronises the device).  NULL is a no-op. */
+void d4orm_batch_destroy(d4orm_batch *batch);
+
+/* One-shot convenience: create (no autotuning), solve, destroy. */
+d4orm_status d4orm_solve_batched(d4orm_problem *const *problems, int count, const d4orm_params *params,
+                                 const d4orm_budget *budget, float *const *u_out_dev, d4orm_result *out_host,
+                                 void *stream);
+
 /* The sample noise eps of Eq. (12) exactly as the step kernels regenerate
  * it: eps_dev[count][T][n][d_u] for samples j0..j0+count-1 of (iter,
  * step_i).  Element e = t*d_u + d of robot k's stream, quad q = e/4, takes

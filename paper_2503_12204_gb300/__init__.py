@@ -39,7 +39,9 @@ EXPORTS = (
     "d4orm_problem_rollout_kernel", "d4orm_rollout", "d4orm_denoise_step",
     "d4orm_denoise_step_timed", "d4orm_denoise_step_noalloc", "d4orm_solve",
     "d4orm_sample_noise", "d4orm_philox4x32_10", "d4orm_status_string", "d4orm_last_error",
+    "d4orm_batch_create", "d4orm_batch_solve", "d4orm_batch_info", "d4orm_batch_destroy", "d4orm_solve_batched",
 )
+BATCH_MAX_SAMPLES = 8192
 
 
 class D4ormError(RuntimeError):
@@ -118,6 +120,18 @@ def _load() -> ctypes.CDLL:
     lib.d4orm_sample_noise.restype = i
     lib.d4orm_philox4x32_10.argtypes = [vp, u32, u32, i, vp, vp]
     lib.d4orm_philox4x32_10.restype = i
+    PP = ctypes.POINTER(vp)
+    lib.d4orm_batch_create.argtypes = [PP, i, ctypes.POINTER(_Params), i, ctypes.POINTER(vp)]
+    lib.d4orm_batch_create.restype = i
+    lib.d4orm_batch_solve.argtypes = [vp, ctypes.POINTER(_Budget), PP, PP, ctypes.POINTER(_Result), vp]
+    lib.d4orm_batch_solve.restype = i
+    lib.d4orm_batch_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_float)]
+    lib.d4orm_batch_info.restype = i
+    lib.d4orm_batch_destroy.argtypes = [vp]
+    lib.d4orm_batch_destroy.restype = None
+    lib.d4orm_solve_batched.argtypes = [PP, i, ctypes.POINTER(_Params), ctypes.POINTER(_Budget), PP,
+                                        ctypes.POINTER(_Result), vp]
+    lib.d4orm_solve_batched.restype = i
     lib.d4orm_status_string.argtypes = [i]
     lib.d4orm_status_string.restype = ctypes.c_char_p
     lib.d4orm_last_error.argtypes = []
@@ -282,6 +296,57 @@ def d4orm_sample_noise(handle, params: Params, iter: int, step_i: int, j0: int, 
 def d4orm_philox4x32_10(ctr_dev, key0: int, key1: int, count: int, out_dev, stream=None) -> None:
     _check(lib.d4orm_philox4x32_10(_ptr(ctr_dev), key0 & 0xFFFFFFFF, key1 & 0xFFFFFFFF, count, _ptr(out_dev),
                                    _stream(stream)))
+
+
+def _ptr_array(items):
+    arr = (ctypes.c_void_p * len(items))()
+    for b, x in enumerate(items):
+        p = _ptr(x)
+        arr[b] = p.value if p is not None else None
+    return arr
+
+
+def _results(res, count):
+    return [dict(verdict=_verdict(r.verdict), iters_run=r.iters_run, first_success_iter=r.first_success_iter,
+                 ms_to_success=r.ms_to_success, ms_total=r.ms_total) for r in list(res)[:count]]
+
+
+def d4orm_batch_create(handles, params: Params, autotune: bool = False) -> ctypes.c_void_p:
+    """Batch over problem handles (they must outlive the batch)."""
+    hs = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    pc = params.c()
+    out = ctypes.c_void_p()
+    _check(lib.d4orm_batch_create(hs, len(handles), ctypes.byref(pc), int(autotune), ctypes.byref(out)))
+    return out
+
+
+def d4orm_batch_solve(batch, budget: Budget, u_out_devs, du_init_devs=None, stream=None) -> list[dict]:
+    bc = budget.c()
+    outs = _ptr_array(u_out_devs)
+    inits = _ptr_array(du_init_devs) if du_init_devs is not None else None
+    res = (_Result * len(u_out_devs))()
+    _check(lib.d4orm_batch_solve(batch, ctypes.byref(bc), inits, outs, res, _stream(stream)))
+    return _results(res, len(u_out_devs))
+
+
+def d4orm_batch_info(batch) -> dict:
+    t, c = ctypes.c_int(), ctypes.c_int()
+    ms = (ctypes.c_float * 3)()
+    _check(lib.d4orm_batch_info(batch, ctypes.byref(t), ctypes.byref(c), ms))
+    return dict(threads_per_cta=t.value, ctas=c.value, tuned_ms=list(ms))
+
+
+def d4orm_batch_destroy(batch) -> None:
+    lib.d4orm_batch_destroy(batch)
+
+
+def d4orm_solve_batched(handles, params: Params, budget: Budget, u_out_devs, stream=None) -> list[dict]:
+    hs = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    pc, bc = params.c(), budget.c()
+    res = (_Result * len(handles))()
+    _check(lib.d4orm_solve_batched(hs, len(handles), ctypes.byref(pc), ctypes.byref(bc), _ptr_array(u_out_devs),
+                                   res, _stream(stream)))
+    return _results(res, len(handles))
 
 
 def d4orm_status_string(status: int) -> str:

@@ -647,6 +647,8 @@ d4orm_status validate_step_args(const d4orm_problem* P, const d4orm_params* para
     return D4ORM_OK;
 }
 
+d4orm_status validate_params(const d4orm_problem* P, const d4orm_params* params) { return check_params(P, params); }
+
 DevStep make_step_consts(const d4orm_params* params, int iter, int step_i)
 {
     std::vector<double> abar;

@@ -119,6 +119,14 @@ __device__ __forceinline__ uint32_t iter_word(const DevStep& S, const int* it_de
 
 __device__ __forceinline__ float clampf(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
 
+// Device-wide nanosecond clock.
+__device__ __forceinline__ long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return (long long)t;
+}
+
 // Square root on the special-function unit (relative error ~2^-23): used
 // for the Eq. (4) distance, which enters a sum checked to 1e-3.
 __device__ __forceinline__ float sqrt_approx(float x)

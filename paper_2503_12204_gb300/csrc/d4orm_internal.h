@@ -64,10 +64,47 @@ cudaError_t launch_sample_noise(const DevProblem& P, const DevStep& S, int j0, i
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t key0, uint32_t key1, int count, uint32_t* out,
                           cudaStream_t st);
 
+// ---------------------------------------------------------------------------
+// K5: batched persistent solver (k_batched.cu)
+// ---------------------------------------------------------------------------
+constexpr int kBatchMaxThreads = 512;
+
+struct BatchInstance {
+    float* tau_u;          // [T][n][d_u] plan workspace
+    float* du0;            // deformation ping
+    float* du1;            // deformation pong
+    float* u_out;          // caller's output plan
+    const float* du_init;  // nullable warm-start deformation at start_step
+};
+
+struct BatchConsts {
+    int count, N, K, max_iters, stop_on_success, start_step;
+    int ctrl_cap, n_cap;   // shared-memory capacities (floats; multiples of 4)
+    uint32_t rk0[10], rk1[10];
+    uint32_t tag_base;
+    float w_safe, inv_lambda;
+};
+
+struct BatchResult {
+    d4orm_verdict verdict;
+    int iters_run;
+    int first_success_iter;
+    long long ns_to_success;  // device clock from the instance's start; -1 if none
+    long long ns_total;       // device clock of the instance's solve
+};
+
+size_t batched_smem_bytes(const BatchConsts& C);
+cudaError_t prepare_batched();
+int batched_ctas_per_sm(int threads, size_t smem);
+cudaError_t launch_batched(const DevProblem* probs, const BatchInstance* insts, const int* order,
+                           const float4* sched, const BatchConsts& C, int* queue, BatchResult* results, int grid,
+                           int threads, cudaStream_t st);
+
 // Shared host-side helpers defined in d4orm_capi.cu.
 d4orm_status validate_step_args(const d4orm_problem* P, const d4orm_params* params, int iter, int step_i,
                                 const float* u_base_dev, const float* du_in_dev, const float* du_out_dev);
 DevStep make_step_consts(const d4orm_params* params, int iter, int step_i);
+d4orm_status validate_params(const d4orm_problem* P, const d4orm_params* params);
 const DevProblem& dev_problem(const d4orm_problem* P);
 int rollout_kernel_choice(const d4orm_problem* P);
 d4orm_status set_error(d4orm_status s, const char* msg);

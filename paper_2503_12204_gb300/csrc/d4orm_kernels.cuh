@@ -1,0 +1,335 @@
+// d4orm_kernels.cuh -- device functions shared by the single-problem kernels
+// and the batched persistent solver: the per-sample rollout + fitness of one
+// lane segment, the one-warp iteration end (apply, rollout, verdict), and the
+// block-wide batch softmax with weight compaction.
+#pragma once
+
+#include <cmath>
+
+#include "d4orm_device.cuh"
+#include "d4orm.h"
+
+namespace d4orm {
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, off));
+    return v;
+}
+
+template <bool MAX>
+__device__ float block_reduce(float v, float* sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = MAX ? warp_max(v) : warp_sum(v);
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < nw ? sh[lane] : (MAX ? -INFINITY : 0.0f);
+        v = MAX ? warp_max(v) : warp_sum(v);
+        if (lane == 0) sh[32] = v;
+    }
+    __syncthreads();
+    const float r = sh[32];
+    __syncthreads();
+    return r;
+}
+
+// Samples whose unnormalised weight exp(l_j - max l) falls below 2^-36
+// are left out of the weighted sum: together they move it by at most
+// N * 2^-36 * max|eps| / Z (under 1e-6 of the largest weight for N <= 65536),
+// below the rounding of the binary32 sum, and typically most samples of a
+// batch are that far below the best one, so the noise they would need is
+// never regenerated.
+constexpr float kLogWeightCut = -24.953298f;  // -36 ln 2
+
+// ---------------------------------------------------------------------------
+// Batch normalisation (Sec. IV-C) + temperature softmax (Eq. (6)) of the N
+// rewards in `fitness` (global or shared memory), by the whole thread block:
+// writes the ordered (weight, index) list of the samples that carry weight
+// and its length.  sh[33], scan[33]: shared scratch.  VR > 0 keeps each
+// thread's (at most VR) values in registers.
+// ---------------------------------------------------------------------------
+template <int VR>
+__device__ __forceinline__ void softmax_block(const float* __restrict__ fitness, int N, float inv_lambda,
+                                              float2* __restrict__ list, int* __restrict__ count,
+                                              float* __restrict__ stats, float* sh, int* scan)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    // contiguous ranges keep the compacted list in sample order
+    const int per = (N + nt - 1) / nt;
+    const int j0 = min(N, tid * per), j1 = min(N, j0 + per);
+    const int cnt = j1 - j0;
+    constexpr int R = VR > 0 ? VR : 1;
+    float r[R];
+    if constexpr (VR > 0) {
+#pragma unroll
+        for (int i = 0; i < VR; ++i) r[i] = i < cnt ? fitness[j0 + i] : 0.0f;
+    }
+    // apply f to every value of this thread's range, in order
+    auto each = [&](auto&& f) {
+        if constexpr (VR > 0) {
+#pragma unroll
+            for (int i = 0; i < VR; ++i)
+                if (i < cnt) f(i, r[i]);
+        } else {
+            for (int i = 0; i < cnt; ++i) f(i, fitness[j0 + i]);
+        }
+    };
+    float s = 0.0f;
+    each([&](int, float x) { s += x; });
+    const float mu = block_reduce<false>(s, sh) / (float)N;
+    float v = 0.0f;
+    each([&](int, float x) {
+        const float d = x - mu;
+        v = fmaf(d, d, v);
+    });
+    const float sd = sqrtf(block_reduce<false>(v, sh) / (float)N);
+    const bool degenerate = !(sd > 1e-12f * fmaxf(1.0f, fabsf(mu)));
+    const float scale = degenerate ? 0.0f : inv_lambda / sd;
+    float m = -INFINITY;
+    each([&](int, float x) { m = fmaxf(m, (x - mu) * scale); });
+    m = block_reduce<true>(m, sh);
+    float z = 0.0f;
+    int kept = 0;
+    each([&](int, float x) {
+        const float l = (x - mu) * scale - m;
+        z += expf(l);
+        kept += l >= kLogWeightCut ? 1 : 0;
+    });
+    const float Z = block_reduce<false>(z, sh);
+    const float invZ = 1.0f / Z;
+    // exclusive scan of the per-thread survivor counts
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    int incl = kept;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int o = __shfl_up_sync(kFull, incl, off);
+        if (lane >= off) incl += o;
+    }
+    if (lane == 31) scan[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int t = lane < nw ? scan[lane] : 0;
+        int ti = t;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int o = __shfl_up_sync(kFull, ti, off);
+            if (lane >= off) ti += o;
+        }
+        if (lane < nw) scan[lane] = ti - t;
+        if (lane == 31) scan[32] = ti;
+    }
+    __syncthreads();
+    int pos = scan[warp] + incl - kept;
+    each([&](int i, float x) {
+        const float l = (x - mu) * scale - m;
+        if (l >= kLogWeightCut) list[pos++] = make_float2(expf(l) * invZ, __int_as_float(j0 + i));
+    });
+    if (tid == 0) {
+        *count = scan[32];
+        if (stats) {
+            stats[0] = mu;
+            stats[1] = sd;
+            stats[2] = m;
+            stats[3] = Z;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One sample per aligned segment of SEG lanes (robot k = lane % SEG), all 32
+// lanes of the warp calling together: Eq. (12) sample, Eq. (1) rollout and
+// Eq. (3)-(5) fitness of sample j.  sM holds the mean controls
+// M[t][k][d] = u_base + c_i dU_i.  Returns the sample's fitness (already
+// divided by nT) on every lane of the segment.  Shared by the single-problem
+// kernel and the batched solver.
+// ---------------------------------------------------------------------------
+template <int DYN, int SEG>
+__device__ __forceinline__ float sample_fitness_segment(const DevProblem& P, const DevStep& S,
+                                                        const float* __restrict__ sM, uint32_t c3, int j)
+{
+    using D = DynDims<DYN>;
+    constexpr int DX = D::DX, DU = D::DU, DP = D::DP;
+    const int lane = threadIdx.x & 31;
+    const int k = lane & (SEG - 1);
+    const int seg_base = lane & ~(SEG - 1);
+    const bool robot = k < P.n;
+    const int kr = robot ? k : P.n - 1;
+
+    float x[DX];
+    load_start<DYN>(x, P, k);
+    float g[DP];
+#pragma unroll
+    for (int d = 0; d < DP; ++d) g[d] = P.goal[kr * 3 + d];
+    const float inv_d0 = P.inv_d0[kr];
+    const float w_safe = S.w_safe;
+    const int rowM = P.n * DU;
+    const float* Mk = sM + kr * DU;
+    float acc = 0.0f;
+    // pair (k, k+s mod SEG) exists when both robots are real
+    bool pair_ok[SEG / 2 > 0 ? SEG / 2 : 1];
+#pragma unroll
+    for (int s = 1; s <= SEG / 2; ++s) pair_ok[s - 1] = robot && (((k + s) & (SEG - 1)) < P.n);
+
+    for (int t0 = 0; t0 < P.T; t0 += 4) {
+        float eps[4 * DU];
+        const uint32_t q0 = (uint32_t)(t0 * DU) >> 2;
+#pragma unroll
+        for (int c = 0; c < DU; ++c) noise_quad(S, c3, q0 + c, (uint32_t)j, (uint32_t)k, &eps[4 * c]);
+#pragma unroll
+        for (int tt = 0; tt < 4; ++tt) {
+            const int t = t0 + tt;
+            if (t < P.T) {  // uniform across the warp
+                float u[DU];
+#pragma unroll
+                for (int d = 0; d < DU; ++d)
+                    u[d] = clampf(fmaf(S.sigma, eps[tt * DU + d], Mk[t * rowM + d]), P.u_lo[d], P.u_hi[d]);
+                integrate<DYN>(x, u, P);
+                // Eq. (4): goal term
+                float dg2 = 0.0f;
+#pragma unroll
+                for (int d = 0; d < DP; ++d) {
+                    const float e = x[d] - g[d];
+                    dg2 = fmaf(e, e, dg2);
+                }
+                // Eq. (5): any partner inside 2R+eps.  Each unordered pair
+                // is evaluated once: lane k tests partner k+s (mod SEG) for
+                // s = 1..SEG/2, and a ballot hands the flag to the partner
+                // (for s = SEG/2 both lanes of the pair test it).
+                bool hit = false;
+#pragma unroll
+                for (int s = 1; s <= SEG / 2; ++s) {
+                    const int src = seg_base + ((k + s) & (SEG - 1));
+                    float d2 = 0.0f;
+#pragma unroll
+                    for (int d = 0; d < DP; ++d) {
+                        const float e = x[d] - __shfl_sync(kFull, x[d], src);
+                        d2 = fmaf(e, e, d2);
+                    }
+                    const bool h = pair_ok[s - 1] & (d2 <= P.thr2);
+                    hit |= h;
+                    if (2 * s != SEG) {
+                        const unsigned m = __ballot_sync(kFull, h);
+                        hit |= (m >> (seg_base + ((k - s) & (SEG - 1)))) & 1u;
+                    }
+                }
+                if (robot) acc += (1.0f - sqrt_approx(dg2) * inv_d0) - (hit ? w_safe : 0.0f);
+            }
+        }
+    }
+    acc = seg_sum<SEG>(acc);
+    return acc * P.inv_nT;
+}
+
+// ---------------------------------------------------------------------------
+// Iteration end of Algorithm 2 on one warp (robots in lanes): u = clip(u_base
+// + dU_0) (du0 nullable; u_out nullable, may alias u_base), rollout from S
+// (states nullable, [T+1][n][d_x]), and the Eq. (1)/(2) verdict written by
+// lane 0 to *verdict (nullable).
+// ---------------------------------------------------------------------------
+template <int DYN>
+__device__ __forceinline__ void apply_rollout_verdict_warp(const DevProblem& P, float w_safe, const float* u_base,
+                                                           const float* du0, float* u_out, float* states,
+                                                           d4orm_verdict* verdict)
+{
+    using D = DynDims<DYN>;
+    constexpr int DX = D::DX, DU = D::DU, DP = D::DP;
+    const int k = threadIdx.x & 31;
+    const bool robot = k < P.n;
+    const int kr = robot ? k : P.n - 1;
+    float x[DX];
+    load_start<DYN>(x, P, k);
+    float g[DP];
+#pragma unroll
+    for (int d = 0; d < DP; ++d) g[d] = P.goal[kr * 3 + d];
+    const float inv_d0 = P.inv_d0[kr];
+
+    auto pair_min = [&](float cur) {
+        float m = cur;
+        for (int s = 1; s < 32; ++s) {
+            float d2 = 0.0f;
+#pragma unroll
+            for (int d = 0; d < DP; ++d) {
+                const float e = x[d] - __shfl_xor_sync(kFull, x[d], s);
+                d2 = fmaf(e, e, d2);
+            }
+            if (((k ^ s) < P.n) && robot) m = fminf(m, d2);
+        }
+        return m;
+    };
+    if (states && robot)
+        for (int c = 0; c < DX; ++c) states[(size_t)k * DX + c] = x[c];
+    float min_d2 = pair_min(INFINITY);
+    float acc = 0.0f;
+    int at_goal = 0;
+    float dg2 = 0.0f;
+    for (int t = 0; t < P.T; ++t) {
+        float u[DU];
+#pragma unroll
+        for (int d = 0; d < DU; ++d) {
+            const size_t idx = ((size_t)t * P.n + kr) * DU + d;
+            const float v = clampf(u_base[idx] + (du0 ? du0[idx] : 0.0f), P.u_lo[d], P.u_hi[d]);
+            u[d] = v;
+            if (u_out && robot) u_out[idx] = v;
+        }
+        integrate<DYN>(x, u, P);
+        if (states && robot)
+            for (int c = 0; c < DX; ++c) states[((size_t)(t + 1) * P.n + k) * DX + c] = x[c];
+        dg2 = 0.0f;
+#pragma unroll
+        for (int d = 0; d < DP; ++d) {
+            const float e = x[d] - g[d];
+            dg2 = fmaf(e, e, dg2);
+        }
+        bool hit = false;
+        float m = INFINITY;
+        for (int s = 1; s < 32; ++s) {
+            float d2 = 0.0f;
+#pragma unroll
+            for (int d = 0; d < DP; ++d) {
+                const float e = x[d] - __shfl_xor_sync(kFull, x[d], s);
+                d2 = fmaf(e, e, d2);
+            }
+            if ((k ^ s) < P.n) {
+                hit |= d2 <= P.thr2;
+                m = fminf(m, d2);
+            }
+        }
+        if (robot) {
+            min_d2 = fminf(min_d2, m);
+            acc += (1.0f - sqrtf(dg2) * inv_d0) - (hit ? w_safe : 0.0f);
+            at_goal += dg2 <= P.tol2 ? 1 : 0;
+        }
+    }
+    int reached = (!robot || dg2 <= P.tol2) ? 1 : 0;
+    float acc_s = acc;
+    int goal_s = at_goal;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        acc_s += __shfl_xor_sync(kFull, acc_s, off);
+        goal_s += __shfl_xor_sync(kFull, goal_s, off);
+        min_d2 = fminf(min_d2, __shfl_xor_sync(kFull, min_d2, off));
+        reached &= __shfl_xor_sync(kFull, reached, off);
+    }
+    if (k == 0) {
+        if (verdict) {
+            d4orm_verdict v;
+            v.collision_free = (P.n < 2 || min_d2 > P.safe2) ? 1 : 0;
+            v.goal_reached = reached;
+            v.reward = acc_s * P.inv_nT;
+            v.objective = (float)goal_s * P.inv_nT;
+            v.min_pair_dist = P.n < 2 ? 1e30f : sqrtf(min_d2);
+            *verdict = v;
+        }
+    }
+}
+
+}  // namespace d4orm

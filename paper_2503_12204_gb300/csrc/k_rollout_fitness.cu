@@ -21,6 +21,7 @@
 #include <cmath>
 
 #include "d4orm_internal.h"
+#include "d4orm_kernels.cuh"
 
 namespace d4orm {
 
@@ -31,8 +32,7 @@ __global__ void __launch_bounds__(kK2Threads)
 k_rollout_fitness(const DevProblem P, const DevStep S, const float* __restrict__ u_base,
                   const float* __restrict__ du_in, float* __restrict__ fitness, const int* __restrict__ it_dev)
 {
-    using D = DynDims<DYN>;
-    constexpr int DX = D::DX, DU = D::DU, DP = D::DP;
+    constexpr int DU = DynDims<DYN>::DU;
     constexpr int SPW = 32 / SEG;  // samples per warp
     extern __shared__ float sM[];  // M[t][k][d]
 
@@ -41,77 +41,10 @@ k_rollout_fitness(const DevProblem P, const DevStep S, const float* __restrict__
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
-    const int k = lane & (SEG - 1);
-    const int seg_base = lane & ~(SEG - 1);
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int j = warp * SPW + lane / SEG;
-    const bool robot = k < P.n;
-    const int kr = robot ? k : P.n - 1;
-    const uint32_t c3 = iter_word(S, it_dev);
-
-    float x[DX];
-    load_start<DYN>(x, P, k);
-    float g[DP];
-#pragma unroll
-    for (int d = 0; d < DP; ++d) g[d] = P.goal[kr * 3 + d];
-    const float inv_d0 = P.inv_d0[kr];
-    const float w_safe = S.w_safe;
-    const int rowM = P.n * DU;
-    const float* Mk = sM + kr * DU;
-    float acc = 0.0f;
-    // pair (k, k+s mod SEG) exists when both robots are real
-    bool pair_ok[SEG / 2 > 0 ? SEG / 2 : 1];
-#pragma unroll
-    for (int s = 1; s <= SEG / 2; ++s) pair_ok[s - 1] = robot && (((k + s) & (SEG - 1)) < P.n);
-
-    for (int t0 = 0; t0 < P.T; t0 += 4) {
-        float eps[4 * DU];
-        const uint32_t q0 = (uint32_t)(t0 * DU) >> 2;
-#pragma unroll
-        for (int c = 0; c < DU; ++c) noise_quad(S, c3, q0 + c, (uint32_t)j, (uint32_t)k, &eps[4 * c]);
-#pragma unroll
-        for (int tt = 0; tt < 4; ++tt) {
-            const int t = t0 + tt;
-            if (t < P.T) {  // uniform across the warp
-                float u[DU];
-#pragma unroll
-                for (int d = 0; d < DU; ++d)
-                    u[d] = clampf(fmaf(S.sigma, eps[tt * DU + d], Mk[t * rowM + d]), P.u_lo[d], P.u_hi[d]);
-                integrate<DYN>(x, u, P);
-                // Eq. (4): goal term
-                float dg2 = 0.0f;
-#pragma unroll
-                for (int d = 0; d < DP; ++d) {
-                    const float e = x[d] - g[d];
-                    dg2 = fmaf(e, e, dg2);
-                }
-                // Eq. (5): any partner inside 2R+eps.  Each unordered pair
-                // is evaluated once: lane k tests partner k+s (mod SEG) for
-                // s = 1..SEG/2, and a ballot hands the flag to the partner
-                // (for s = SEG/2 both lanes of the pair test it).
-                bool hit = false;
-#pragma unroll
-                for (int s = 1; s <= SEG / 2; ++s) {
-                    const int src = seg_base + ((k + s) & (SEG - 1));
-                    float d2 = 0.0f;
-#pragma unroll
-                    for (int d = 0; d < DP; ++d) {
-                        const float e = x[d] - __shfl_sync(kFull, x[d], src);
-                        d2 = fmaf(e, e, d2);
-                    }
-                    const bool h = pair_ok[s - 1] & (d2 <= P.thr2);
-                    hit |= h;
-                    if (2 * s != SEG) {
-                        const unsigned m = __ballot_sync(kFull, h);
-                        hit |= (m >> (seg_base + ((k - s) & (SEG - 1)))) & 1u;
-                    }
-                }
-                if (robot) acc += (1.0f - sqrt_approx(dg2) * inv_d0) - (hit ? w_safe : 0.0f);
-            }
-        }
-    }
-    acc = seg_sum<SEG>(acc);
-    if (k == 0 && j < S.N) fitness[j] = acc * P.inv_nT;
+    const float f = sample_fitness_segment<DYN, SEG>(P, S, sM, iter_word(S, it_dev), j);
+    if ((lane & (SEG - 1)) == 0 && j < S.N) fitness[j] = f;
 }
 
 // Opt in to up to 200 KB of dynamic shared memory (mean controls of the

@@ -19,49 +19,11 @@
 #include <cmath>
 
 #include "d4orm_internal.h"
+#include "d4orm_kernels.cuh"
 
 namespace d4orm {
 
 constexpr int kSoftmaxThreads = 1024;
-
-__device__ __forceinline__ float warp_sum(float v)
-{
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-    return v;
-}
-__device__ __forceinline__ float warp_max(float v)
-{
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, off));
-    return v;
-}
-
-template <bool MAX>
-__device__ float block_reduce(float v, float* sh)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    v = MAX ? warp_max(v) : warp_sum(v);
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        v = lane < nw ? sh[lane] : (MAX ? -INFINITY : 0.0f);
-        v = MAX ? warp_max(v) : warp_sum(v);
-        if (lane == 0) sh[32] = v;
-    }
-    __syncthreads();
-    const float r = sh[32];
-    __syncthreads();
-    return r;
-}
-
-// Samples whose unnormalised weight exp(l_j - max l) falls below 2^-36
-// are left out of the weighted sum: together they move it by at most
-// N * 2^-36 * max|eps| / Z (under 1e-6 of the largest weight for N <= 65536),
-// below the rounding of the binary32 sum, and typically most samples of a
-// batch are that far below the best one, so the noise they would need is
-// never regenerated.
-constexpr float kLogWeightCut = -24.953298f;  // -36 ln 2
 
 // VR > 0: each thread keeps its (at most VR) fitness values in registers;
 // VR == 0: the values are re-read from global memory (L1) on every pass.
@@ -72,86 +34,7 @@ k_softmax_weights(const float* __restrict__ fitness, int N, float inv_lambda, fl
 {
     __shared__ float sh[33];
     __shared__ int scan[33];
-    const int tid = threadIdx.x, nt = blockDim.x;
-    // contiguous ranges keep the compacted list in sample order
-    const int per = (N + nt - 1) / nt;
-    const int j0 = min(N, tid * per), j1 = min(N, j0 + per);
-    const int cnt = j1 - j0;
-    constexpr int R = VR > 0 ? VR : 1;
-    float r[R];
-    if constexpr (VR > 0) {
-#pragma unroll
-        for (int i = 0; i < VR; ++i) r[i] = i < cnt ? fitness[j0 + i] : 0.0f;
-    }
-    // apply f to every value of this thread's range, in order
-    auto each = [&](auto&& f) {
-        if constexpr (VR > 0) {
-#pragma unroll
-            for (int i = 0; i < VR; ++i)
-                if (i < cnt) f(i, r[i]);
-        } else {
-            for (int i = 0; i < cnt; ++i) f(i, fitness[j0 + i]);
-        }
-    };
-    float s = 0.0f;
-    each([&](int, float x) { s += x; });
-    const float mu = block_reduce<false>(s, sh) / (float)N;
-    float v = 0.0f;
-    each([&](int, float x) {
-        const float d = x - mu;
-        v = fmaf(d, d, v);
-    });
-    const float sd = sqrtf(block_reduce<false>(v, sh) / (float)N);
-    const bool degenerate = !(sd > 1e-12f * fmaxf(1.0f, fabsf(mu)));
-    const float scale = degenerate ? 0.0f : inv_lambda / sd;
-    float m = -INFINITY;
-    each([&](int, float x) { m = fmaxf(m, (x - mu) * scale); });
-    m = block_reduce<true>(m, sh);
-    float z = 0.0f;
-    int kept = 0;
-    each([&](int, float x) {
-        const float l = (x - mu) * scale - m;
-        z += expf(l);
-        kept += l >= kLogWeightCut ? 1 : 0;
-    });
-    const float Z = block_reduce<false>(z, sh);
-    const float invZ = 1.0f / Z;
-    // exclusive scan of the per-thread survivor counts
-    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    int incl = kept;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int o = __shfl_up_sync(kFull, incl, off);
-        if (lane >= off) incl += o;
-    }
-    if (lane == 31) scan[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        int t = lane < nw ? scan[lane] : 0;
-        int ti = t;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int o = __shfl_up_sync(kFull, ti, off);
-            if (lane >= off) ti += o;
-        }
-        if (lane < nw) scan[lane] = ti - t;
-        if (lane == 31) scan[32] = ti;
-    }
-    __syncthreads();
-    int pos = scan[warp] + incl - kept;
-    each([&](int i, float x) {
-        const float l = (x - mu) * scale - m;
-        if (l >= kLogWeightCut) list[pos++] = make_float2(expf(l) * invZ, __int_as_float(j0 + i));
-    });
-    if (tid == 0) {
-        *count = scan[32];
-        if (stats) {
-            stats[0] = mu;
-            stats[1] = sd;
-            stats[2] = m;
-            stats[3] = Z;
-        }
-    }
+    softmax_block<VR>(fitness, N, inv_lambda, list, count, stats, sh, scan);
 }
 
 constexpr int kWSRows = 8;

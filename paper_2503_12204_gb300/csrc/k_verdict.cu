@@ -12,6 +12,7 @@
 #include <cmath>
 
 #include "d4orm_internal.h"
+#include "d4orm_kernels.cuh"
 
 namespace d4orm {
 
@@ -20,97 +21,8 @@ __global__ void __launch_bounds__(32)
 k_apply_rollout_verdict(const DevProblem P, float w_safe, const float* u_base, const float* du0, float* u_out,
                         float* __restrict__ states, d4orm_verdict* __restrict__ verdict, int* it_inc)
 {
-    using D = DynDims<DYN>;
-    constexpr int DX = D::DX, DU = D::DU, DP = D::DP;
-    const int k = threadIdx.x;
-    const bool robot = k < P.n;
-    const int kr = robot ? k : P.n - 1;
-    float x[DX];
-    load_start<DYN>(x, P, k);
-    float g[DP];
-#pragma unroll
-    for (int d = 0; d < DP; ++d) g[d] = P.goal[kr * 3 + d];
-    const float inv_d0 = P.inv_d0[kr];
-
-    auto pair_min = [&](float cur) {
-        float m = cur;
-        for (int s = 1; s < 32; ++s) {
-            float d2 = 0.0f;
-#pragma unroll
-            for (int d = 0; d < DP; ++d) {
-                const float e = x[d] - __shfl_xor_sync(kFull, x[d], s);
-                d2 = fmaf(e, e, d2);
-            }
-            if (((k ^ s) < P.n) && robot) m = fminf(m, d2);
-        }
-        return m;
-    };
-    if (states && robot)
-        for (int c = 0; c < DX; ++c) states[(size_t)k * DX + c] = x[c];
-    float min_d2 = pair_min(INFINITY);
-    float acc = 0.0f;
-    int at_goal = 0;
-    float dg2 = 0.0f;
-    for (int t = 0; t < P.T; ++t) {
-        float u[DU];
-#pragma unroll
-        for (int d = 0; d < DU; ++d) {
-            const size_t idx = ((size_t)t * P.n + kr) * DU + d;
-            const float v = clampf(u_base[idx] + (du0 ? du0[idx] : 0.0f), P.u_lo[d], P.u_hi[d]);
-            u[d] = v;
-            if (u_out && robot) u_out[idx] = v;
-        }
-        integrate<DYN>(x, u, P);
-        if (states && robot)
-            for (int c = 0; c < DX; ++c) states[((size_t)(t + 1) * P.n + k) * DX + c] = x[c];
-        dg2 = 0.0f;
-#pragma unroll
-        for (int d = 0; d < DP; ++d) {
-            const float e = x[d] - g[d];
-            dg2 = fmaf(e, e, dg2);
-        }
-        bool hit = false;
-        float m = INFINITY;
-        for (int s = 1; s < 32; ++s) {
-            float d2 = 0.0f;
-#pragma unroll
-            for (int d = 0; d < DP; ++d) {
-                const float e = x[d] - __shfl_xor_sync(kFull, x[d], s);
-                d2 = fmaf(e, e, d2);
-            }
-            if ((k ^ s) < P.n) {
-                hit |= d2 <= P.thr2;
-                m = fminf(m, d2);
-            }
-        }
-        if (robot) {
-            min_d2 = fminf(min_d2, m);
-            acc += (1.0f - sqrtf(dg2) * inv_d0) - (hit ? w_safe : 0.0f);
-            at_goal += dg2 <= P.tol2 ? 1 : 0;
-        }
-    }
-    int reached = (!robot || dg2 <= P.tol2) ? 1 : 0;
-    float acc_s = acc;
-    int goal_s = at_goal;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        acc_s += __shfl_xor_sync(kFull, acc_s, off);
-        goal_s += __shfl_xor_sync(kFull, goal_s, off);
-        min_d2 = fminf(min_d2, __shfl_xor_sync(kFull, min_d2, off));
-        reached &= __shfl_xor_sync(kFull, reached, off);
-    }
-    if (k == 0) {
-        if (verdict) {
-            d4orm_verdict v;
-            v.collision_free = (P.n < 2 || min_d2 > P.safe2) ? 1 : 0;
-            v.goal_reached = reached;
-            v.reward = acc_s * P.inv_nT;
-            v.objective = (float)goal_s * P.inv_nT;
-            v.min_pair_dist = P.n < 2 ? 1e30f : sqrtf(min_d2);
-            *verdict = v;
-        }
-        if (it_inc) *it_inc += 1;
-    }
+    apply_rollout_verdict_warp<DYN>(P, w_safe, u_base, du0, u_out, states, verdict);
+    if (threadIdx.x == 0 && it_inc) *it_inc += 1;
 }
 
 cudaError_t launch_apply_rollout_verdict(const DevProblem& P, float w_safe, const float* u_base, const float* du0,

@@ -1,0 +1,126 @@
+"""GPU parity of the batched persistent solve (one launch over ragged
+problems) against the single-problem path and the FP64 oracle.
+
+Problem b of a batch draws its noise with tag params.instance_tag + b, so a
+single-problem d4orm_solve with that tag evaluates the same samples; the
+two paths differ only in the order of floating-point reductions (softmax
+statistics, weighted sums), so their plans agree to rounding amplified by
+the softmax over a few steps: checked at 1e-3 of the plan's scale, with
+verdicts equal.  Each batched plan is also re-judged by the oracle (FP64
+rollout of the GPU's own plan): identical verdict flags away from the
+thresholds.
+"""
+import numpy as np
+import pytest
+
+import scenarios
+from helpers import gpu_params, oracle_problem, round_instance
+
+pytestmark = pytest.mark.gpu
+
+DELTA = 2e-4
+
+
+@pytest.fixture(scope="module")
+def torch():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("CUDA device required")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def g(torch):
+    from helpers import build_library
+    build_library()
+    import paper_2503_12204_gb300 as g
+    return g
+
+
+def _mixed(count, seed, N, K):
+    batch = scenarios.mixed_batch(count=count, seed=seed, N=N)
+    out = []
+    for inst in batch:
+        inst.K = K
+        out.append(round_instance(inst))
+    return out
+
+
+@pytest.mark.parametrize("autotune", [False, True])
+def test_batched_matches_single_solves(torch, g, oracle_lib, autotune):
+    insts = _mixed(12, seed=5, N=256, K=6)
+    probs = [g.Problem(i) for i in insts]
+    params = g.Params(n_samples=256, n_steps=6, seed=3, instance_tag=40)
+    outs = [torch.zeros((i.T, i.n, i.dims[1]), device="cuda") for i in insts]
+    batch = g.d4orm_batch_create([p.handle for p in probs], params, autotune=autotune)
+    info = g.d4orm_batch_info(batch)
+    assert info["threads_per_cta"] in (128, 256, 512) and info["ctas"] >= 1
+    if autotune:
+        assert max(info["tuned_ms"]) > 0
+    res = g.d4orm_batch_solve(batch, g.Budget(max_iters=2), outs)
+    torch.cuda.synchronize()
+    for b, (inst, p) in enumerate(zip(insts, probs)):
+        single = g.Params(n_samples=256, n_steps=6, seed=3, instance_tag=40 + b)
+        u = torch.zeros_like(outs[b])
+        r1 = g.d4orm_solve(p.handle, single, g.Budget(max_iters=2), u)
+        a, s = outs[b].cpu().numpy(), u.cpu().numpy()
+        scale = max(np.abs(s).max(), 1e-3)
+        assert np.abs(a - s).max() <= 1e-3 * scale, (b, np.abs(a - s).max(), scale)
+        assert res[b]["iters_run"] == 2
+        st = oracle_lib.rollout(oracle_problem(oracle_lib, inst), a.astype(np.float64))
+        vo = oracle_lib.verdict(oracle_problem(oracle_lib, inst), inst.w_safe, st)
+        if abs(vo["min_pair_dist"] - 2 * inst.radius) > DELTA:
+            assert res[b]["verdict"]["collision_free"] == vo["collision_free"] == r1["verdict"]["collision_free"]
+        fin = np.linalg.norm(st[-1, :, :inst.dims[2]] - inst.goal[:, :inst.dims[2]], axis=1)
+        if np.all(np.abs(fin - inst.goal_tol) > DELTA):
+            assert res[b]["verdict"]["goal_reached"] == vo["goal_reached"]
+    g.d4orm_batch_destroy(batch)
+
+
+def test_batched_stop_on_success_and_warm_start(torch, g):
+    start = np.array([[-1.5, 0, 0, 0], [1.5, 0, 0, 0]])
+    swap = round_instance(scenarios.Instance("swap", 0, 1, 2, 60, 0.1, 0.2, (-1.0, -1.0), (1.0, 1.0), 1.0, start,
+                                             -start, N=256, K=100, iters=6, seed=0))
+    insts = [swap] + _mixed(5, seed=9, N=256, K=100)
+    probs = [g.Problem(i) for i in insts]
+    params = g.Params(n_samples=256, n_steps=100, seed=0)
+    outs = [torch.zeros((i.T, i.n, i.dims[1]), device="cuda") for i in insts]
+    batch = g.d4orm_batch_create([p.handle for p in probs], params)
+    res = g.d4orm_batch_solve(batch, g.Budget(max_iters=6, stop_on_success=True), outs)
+    assert res[0]["first_success_iter"] >= 0
+    for r in res:
+        if r["first_success_iter"] >= 0:
+            assert r["iters_run"] == r["first_success_iter"] + 1
+            assert r["verdict"]["collision_free"] and r["verdict"]["goal_reached"]
+            assert 0 < r["ms_to_success"] <= r["ms_total"]
+        else:
+            assert r["iters_run"] == 6
+    # warm start from the solved plan's own deformation scale: first iteration runs steps 30..1
+    inits = [torch.zeros_like(o) for o in outs]
+    res2 = g.d4orm_batch_solve(batch, g.Budget(max_iters=1, start_step=30), outs, du_init_devs=inits)
+    assert all(r["iters_run"] == 1 for r in res2)
+    single = g.Params(n_samples=256, n_steps=100, seed=0, instance_tag=0)
+    u = torch.zeros_like(outs[0])
+    g.d4orm_solve(probs[0].handle, single, g.Budget(max_iters=1, start_step=30), u, du_init_dev=inits[0])
+    torch.cuda.synchronize()
+    s = u.cpu().numpy()
+    assert np.abs(outs[0].cpu().numpy() - s).max() <= 1e-3 * max(np.abs(s).max(), 1e-3)
+    g.d4orm_batch_destroy(batch)
+
+
+def test_batched_argument_errors(torch, g):
+    inst = round_instance(scenarios.holo2d_circle_n4())
+    p = g.Problem(inst)
+    with pytest.raises(g.D4ormError) as ei:
+        g.d4orm_batch_create([p.handle], g.Params(n_samples=g.BATCH_MAX_SAMPLES + 1, n_steps=10))
+    assert ei.value.status == 2
+    batch = g.d4orm_batch_create([p.handle], g.Params(n_samples=64, n_steps=10))
+    out = torch.zeros((inst.T, inst.n, 2), device="cuda")
+    with pytest.raises(g.D4ormError):
+        g.d4orm_batch_solve(batch, g.Budget(max_iters=0), [out])
+    with pytest.raises(g.D4ormError) as ei:
+        g.d4orm_batch_solve(batch, g.Budget(max_iters=1, deadline_ms=5.0), [out])
+    assert ei.value.status == 2
+    g.d4orm_batch_destroy(batch)
+    res = g.d4orm_solve_batched([p.handle], g.Params(n_samples=64, n_steps=10), g.Budget(max_iters=1), [out])
+    assert res[0]["iters_run"] == 1
