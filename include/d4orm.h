@@ -286,6 +286,80 @@ d4orm_status d4orm_solve_batched(d4orm_problem *const *problems, int count, cons
                                  const d4orm_budget *budget, float *const *u_out_dev, d4orm_result *out_host,
                                  void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned warm start (not part of the paper, whose method has no learning
+ * component): a set-MLP that maps a team's starts and goals to a control
+ * plan, trained on plans the method itself produced, used to seed the
+ * deformation so that denoising can start at an intermediate step; the
+ * plain method stays the fallback.
+ *
+ * Network, per team (robots padded to n_max, padded rows masked):
+ *   x_k (16 features: start/scale, goal/scale, (goal-start)/scale,
+ *        |goal-start|/scale, 1, zero padding; 3 slots per vector, z = 0 in 2D)
+ *   H1 = relu(x W1' + b1), H2 = relu(H1 W2' + b2), H3 = relu(H2 W3' + b3)
+ *   Pbar = masked mean of H3 over robots
+ *   H4 = relu([H3, Pbar] W4' + b4), H5 = relu(H4 W5' + b5), Y = H5 W6' + b6
+ *   (Y_k = robot k's controls, T * d_u values ordered t-major)
+ * Loss: masked mean squared error against the target plans.  GEMMs run on
+ * the tensor cores in BF16 with FP32 accumulation; parameters are FP32
+ * masters (flat vector: W1, b1, W2, b2, ..., W6, b6; W_l row-major
+ * [out][in]) with BF16 copies; AdamW updates the masters.
+ * ------------------------------------------------------------------------- */
+typedef struct d4orm_warmstart d4orm_warmstart;
+
+typedef struct {
+    int n_max;          /* robots per team (padded), 1..32                    */
+    int T, d_u;         /* plan shape predicted per robot                     */
+    int width;          /* hidden width (multiple of 16, <= 1024)             */
+    int max_batch;      /* teams per forward/training batch                   */
+    uint64_t seed;      /* initialisation (uniform +-1/sqrt(fan_in), zero bias) */
+    float lr, beta1, beta2, eps, weight_decay;   /* AdamW                     */
+    float pos_scale;    /* metres per unit of the position features          */
+} d4orm_warmstart_desc;
+
+/* Create a network with seeded initial weights.  Errors: INVALID_ARG for
+ * shapes out of range; OOM; CUDA. */
+d4orm_status d4orm_warmstart_create(const d4orm_warmstart_desc *desc, d4orm_warmstart **out);
+void d4orm_warmstart_destroy(d4orm_warmstart *ws);
+
+/* Number of FP32 parameters (-1 for NULL). */
+int d4orm_warmstart_param_count(const d4orm_warmstart *ws);
+
+/* Copy the FP32 master parameters to / from host memory (count must equal
+ * the parameter count).  set_params also resets the AdamW state. */
+d4orm_status d4orm_warmstart_get_params(const d4orm_warmstart *ws, float *host, int count);
+d4orm_status d4orm_warmstart_set_params(d4orm_warmstart *ws, const float *host, int count);
+
+/* Forward pass of B teams: x_dev [B][n_max][16], mask_dev [B][n_max],
+ * y_dev [B][n_max][T*d_u].  Asynchronous on `stream`. */
+d4orm_status d4orm_warmstart_forward(d4orm_warmstart *ws, const float *x_dev, const float *mask_dev, int B,
+                                     float *y_dev, void *stream);
+
+/* Forward + masked MSE against y_dev + backward, without updating.
+ * loss_host (nullable; synchronises), grad_dev (nullable) receives the flat
+ * FP32 gradient (parameter layout). */
+d4orm_status d4orm_warmstart_loss_grad(d4orm_warmstart *ws, const float *x_dev, const float *mask_dev,
+                                       const float *y_dev, int B, float *loss_host, float *grad_dev, void *stream);
+
+/* One AdamW training step on B teams.  With idx_dev (int[B]) the teams are
+ * gathered from a dataset x_all [*][n_max][16], mask_all [*][n_max],
+ * y_all [*][n_max][T*d_u]; with idx_dev NULL the first B teams are used.
+ * loss_host (nullable; synchronises) receives the loss before the update. */
+d4orm_status d4orm_warmstart_train_step(d4orm_warmstart *ws, const float *x_all, const float *mask_all,
+                                        const float *y_all, const int *idx_dev, int B, float *loss_host,
+                                        void *stream);
+
+/* Input features of one problem (host): x_host [n_max][16], mask_host [n_max]. */
+d4orm_status d4orm_warmstart_features(const d4orm_problem *problem, int n_max, float pos_scale, float *x_host,
+                                      float *mask_host);
+
+/* Seed for d4orm_solve / d4orm_batch_solve: du_seed_dev [T][n][d_u] =
+ * sqrt(abar_{start_step}) * Y (the network's plan for the problem), so the
+ * first sampled mean at start_step is the predicted plan itself (base plan
+ * zero).  Synchronises `stream`. */
+d4orm_status d4orm_warmstart_predict(d4orm_warmstart *ws, const d4orm_problem *problem, const d4orm_params *params,
+                                     int start_step, float *du_seed_dev, void *stream);
+
 /* The sample noise eps of Eq. (12) exactly as the step kernels regenerate
  * it: eps_dev[count][T][n][d_u] for samples j0..j0+count-1 of (iter,
  * step_i).  Element e = t*d_u + d of robot k's stream, quad q = e/4, takes

@@ -40,7 +40,12 @@ EXPORTS = (
     "d4orm_denoise_step_timed", "d4orm_denoise_step_noalloc", "d4orm_solve",
     "d4orm_sample_noise", "d4orm_philox4x32_10", "d4orm_status_string", "d4orm_last_error",
     "d4orm_batch_create", "d4orm_batch_solve", "d4orm_batch_info", "d4orm_batch_destroy", "d4orm_solve_batched",
+    "d4orm_warmstart_create", "d4orm_warmstart_destroy", "d4orm_warmstart_param_count",
+    "d4orm_warmstart_get_params", "d4orm_warmstart_set_params", "d4orm_warmstart_forward",
+    "d4orm_warmstart_loss_grad", "d4orm_warmstart_train_step", "d4orm_warmstart_features",
+    "d4orm_warmstart_predict",
 )
+WS_FEATURES = 16
 BATCH_MAX_SAMPLES = 8192
 
 
@@ -72,6 +77,15 @@ class _Budget(ctypes.Structure):
     _fields_ = [
         ("max_iters", ctypes.c_int), ("deadline_ms", ctypes.c_double), ("stop_on_success", ctypes.c_int),
         ("start_step", ctypes.c_int),
+    ]
+
+
+class _WsDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_max", ctypes.c_int), ("T", ctypes.c_int), ("d_u", ctypes.c_int), ("width", ctypes.c_int),
+        ("max_batch", ctypes.c_int), ("seed", ctypes.c_uint64), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
+        ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("weight_decay", ctypes.c_float),
+        ("pos_scale", ctypes.c_float),
     ]
 
 
@@ -132,6 +146,27 @@ def _load() -> ctypes.CDLL:
     lib.d4orm_solve_batched.argtypes = [PP, i, ctypes.POINTER(_Params), ctypes.POINTER(_Budget), PP,
                                         ctypes.POINTER(_Result), vp]
     lib.d4orm_solve_batched.restype = i
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.d4orm_warmstart_create.argtypes = [ctypes.POINTER(_WsDesc), ctypes.POINTER(vp)]
+    lib.d4orm_warmstart_create.restype = i
+    lib.d4orm_warmstart_destroy.argtypes = [vp]
+    lib.d4orm_warmstart_destroy.restype = None
+    lib.d4orm_warmstart_param_count.argtypes = [vp]
+    lib.d4orm_warmstart_param_count.restype = i
+    lib.d4orm_warmstart_get_params.argtypes = [vp, fp, i]
+    lib.d4orm_warmstart_get_params.restype = i
+    lib.d4orm_warmstart_set_params.argtypes = [vp, fp, i]
+    lib.d4orm_warmstart_set_params.restype = i
+    lib.d4orm_warmstart_forward.argtypes = [vp, vp, vp, i, vp, vp]
+    lib.d4orm_warmstart_forward.restype = i
+    lib.d4orm_warmstart_loss_grad.argtypes = [vp, vp, vp, vp, i, fp, vp, vp]
+    lib.d4orm_warmstart_loss_grad.restype = i
+    lib.d4orm_warmstart_train_step.argtypes = [vp, vp, vp, vp, vp, i, fp, vp]
+    lib.d4orm_warmstart_train_step.restype = i
+    lib.d4orm_warmstart_features.argtypes = [vp, i, ctypes.c_float, fp, fp]
+    lib.d4orm_warmstart_features.restype = i
+    lib.d4orm_warmstart_predict.argtypes = [vp, vp, ctypes.POINTER(_Params), i, vp, vp]
+    lib.d4orm_warmstart_predict.restype = i
     lib.d4orm_status_string.argtypes = [i]
     lib.d4orm_status_string.restype = ctypes.c_char_p
     lib.d4orm_last_error.argtypes = []
@@ -347,6 +382,90 @@ def d4orm_solve_batched(handles, params: Params, budget: Budget, u_out_devs, str
     _check(lib.d4orm_solve_batched(hs, len(handles), ctypes.byref(pc), ctypes.byref(bc), _ptr_array(u_out_devs),
                                    res, _stream(stream)))
     return _results(res, len(handles))
+
+
+@dataclass
+class WarmStartDesc:
+    """Shape and optimiser settings of the set-MLP (d4orm_warmstart_desc)."""
+    n_max: int = 16
+    T: int = 80
+    d_u: int = 2
+    width: int = 256
+    max_batch: int = 256
+    seed: int = 0
+    lr: float = 1e-3
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-8
+    weight_decay: float = 1e-4
+    pos_scale: float = 5.0
+
+    def c(self) -> _WsDesc:
+        return _WsDesc(self.n_max, self.T, self.d_u, self.width, self.max_batch, self.seed, self.lr, self.beta1,
+                       self.beta2, self.eps, self.weight_decay, self.pos_scale)
+
+
+def d4orm_warmstart_create(desc: WarmStartDesc) -> ctypes.c_void_p:
+    dc = desc.c()
+    out = ctypes.c_void_p()
+    _check(lib.d4orm_warmstart_create(ctypes.byref(dc), ctypes.byref(out)))
+    return out
+
+
+def d4orm_warmstart_destroy(ws) -> None:
+    lib.d4orm_warmstart_destroy(ws)
+
+
+def d4orm_warmstart_param_count(ws) -> int:
+    return lib.d4orm_warmstart_param_count(ws)
+
+
+def d4orm_warmstart_get_params(ws):
+    import numpy as np
+    n = lib.d4orm_warmstart_param_count(ws)
+    out = np.zeros(n, dtype=np.float32)
+    _check(lib.d4orm_warmstart_get_params(ws, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), n))
+    return out
+
+
+def d4orm_warmstart_set_params(ws, params) -> None:
+    import numpy as np
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(lib.d4orm_warmstart_set_params(ws, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), len(p)))
+
+
+def d4orm_warmstart_forward(ws, x_dev, mask_dev, B: int, y_dev, stream=None) -> None:
+    _check(lib.d4orm_warmstart_forward(ws, _ptr(x_dev), _ptr(mask_dev), B, _ptr(y_dev), _stream(stream)))
+
+
+def d4orm_warmstart_loss_grad(ws, x_dev, mask_dev, y_dev, B: int, grad_dev=None, stream=None) -> float:
+    loss = ctypes.c_float()
+    _check(lib.d4orm_warmstart_loss_grad(ws, _ptr(x_dev), _ptr(mask_dev), _ptr(y_dev), B, ctypes.byref(loss),
+                                         _ptr(grad_dev), _stream(stream)))
+    return loss.value
+
+
+def d4orm_warmstart_train_step(ws, x_all, mask_all, y_all, B: int, idx_dev=None, want_loss: bool = True,
+                               stream=None):
+    loss = ctypes.c_float()
+    _check(lib.d4orm_warmstart_train_step(ws, _ptr(x_all), _ptr(mask_all), _ptr(y_all), _ptr(idx_dev), B,
+                                          ctypes.byref(loss) if want_loss else None, _stream(stream)))
+    return loss.value if want_loss else None
+
+
+def d4orm_warmstart_features(handle, n_max: int, pos_scale: float = 5.0):
+    import numpy as np
+    x = np.zeros((n_max, WS_FEATURES), dtype=np.float32)
+    m = np.zeros(n_max, dtype=np.float32)
+    _check(lib.d4orm_warmstart_features(handle, n_max, pos_scale, x.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                        m.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return x, m
+
+
+def d4orm_warmstart_predict(ws, handle, params: Params, start_step: int, du_seed_dev, stream=None) -> None:
+    pc = params.c()
+    _check(lib.d4orm_warmstart_predict(ws, handle, ctypes.byref(pc), start_step, _ptr(du_seed_dev),
+                                       _stream(stream)))
 
 
 def d4orm_status_string(status: int) -> str:

@@ -100,6 +100,41 @@ cudaError_t launch_batched(const DevProblem* probs, const BatchInstance* insts, 
                            const float4* sched, const BatchConsts& C, int* queue, BatchResult* results, int grid,
                            int threads, cudaStream_t st);
 
+// ---------------------------------------------------------------------------
+// Learned warm start: set-MLP kernels (k_setmlp.cu)
+// ---------------------------------------------------------------------------
+// C[m][n] = sum_k A(m, k) * B(n, k), A(m, k) = A[m * a_rs + k * a_cs],
+// B(n, k) = B[n * b_rs + k * b_cs]; epilogue: + bias[n], relu, zero where
+// ref(m, n) <= 0, store to out_f32 / out_bf16 (row stride ldc); with
+// splits > 1, raw partials to partial[split][M][N] instead.
+struct GemmArgs {
+    int M, N, K;
+    long long a_rs, a_cs, b_rs, b_cs;
+    const float* bias;
+    int relu;
+    const void* ref;             // __nv_bfloat16  // relu-gradient mask source, [M][ldc]
+    float* out_f32;
+    void* out_bf16;              // __nv_bfloat16
+    long long ldc;
+    float* partial;
+};
+cudaError_t mlp_gemm(const void* A, bool a_bf16, const void* B, bool b_bf16, const GemmArgs& g, int splits,
+                     cudaStream_t st);
+cudaError_t mlp_sum_partials(const float* partial, int splits, long long MN, float* out, cudaStream_t st);
+cudaError_t mlp_colsum(const float* dY, int M, int N, float* db, cudaStream_t st);
+cudaError_t mlp_pool_concat(const void* H3, const float* mask, int B, int nmax, int W, void* C, cudaStream_t st);
+cudaError_t mlp_pool_concat_bwd(const float* dC, const float* mask, const void* H3, int B, int nmax, int W,
+                                float* dH3, cudaStream_t st);
+cudaError_t mlp_mse(const float* Y, const float* Tgt, const float* mask, int rows, int D, float* dY, float* loss,
+                    cudaStream_t st);
+cudaError_t mlp_adamw(float* p, void* p16, const float* grad, float* m, float* v, long long count, float lr, float b1,
+                      float b2, float eps, float wd, float bc1, float bc2, cudaStream_t st);
+cudaError_t mlp_to_bf16(const float* src, void* dst, long long count, cudaStream_t st);
+cudaError_t mlp_gather_rows(const float* src, const int* idx, int rows_per, int w, long long total_rows, float* dst,
+                            cudaStream_t st);
+cudaError_t mlp_seed_from_output(const float* Y, int n, int T, int d_u, int D, float scale, float* du_seed,
+                                 cudaStream_t st);
+
 // Shared host-side helpers defined in d4orm_capi.cu.
 d4orm_status validate_step_args(const d4orm_problem* P, const d4orm_params* params, int iter, int step_i,
                                 const float* u_base_dev, const float* du_in_dev, const float* du_out_dev);

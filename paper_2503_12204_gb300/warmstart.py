@@ -1,0 +1,238 @@
+"""Learned warm start pipeline: the method generates its own training data,
+the set-MLP learns start/goal -> plan, and the evaluation compares the
+warm-started solve against the plain one on held-out teams.
+
+Every numerical step runs in the library's CUDA kernels through the C ABI:
+the batched persistent solver produces the plans, d4orm_warmstart_train_step
+trains (BF16 tensor-core forward/backward, AdamW), d4orm_warmstart_predict
+seeds the deformation.  This module only orchestrates: it builds problems,
+assembles arrays, and tallies results.
+
+    python -m paper_2503_12204_gb300.warmstart --train 50000 --held-out 1000 --out DIR
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import struct
+import time
+
+import numpy as np
+
+from . import (Budget, Params, Problem, WarmStartDesc, d4orm_batch_create, d4orm_batch_destroy, d4orm_batch_solve,
+               d4orm_warmstart_create, d4orm_warmstart_features, d4orm_warmstart_get_params,
+               d4orm_warmstart_predict, d4orm_warmstart_set_params, d4orm_warmstart_train_step)
+
+MAGIC = b"D4WS"
+
+
+def save_weights(path: str, desc: WarmStartDesc, params: np.ndarray, meta: dict | None = None) -> None:
+    """Flat binary: magic, header length, JSON header (shape + settings), FP32 parameters."""
+    header = json.dumps(dict(desc=desc.__dict__, count=int(len(params)), meta=meta or {})).encode()
+    with open(path, "wb") as f:
+        f.write(MAGIC)
+        f.write(struct.pack("<I", len(header)))
+        f.write(header)
+        f.write(np.ascontiguousarray(params, dtype=np.float32).tobytes())
+
+
+def load_weights(path: str):
+    with open(path, "rb") as f:
+        assert f.read(4) == MAGIC, "not a warm-start weight file"
+        (hl,) = struct.unpack("<I", f.read(4))
+        header = json.loads(f.read(hl))
+        params = np.frombuffer(f.read(), dtype=np.float32).copy()
+    assert len(params) == header["count"]
+    return WarmStartDesc(**header["desc"]), params, header.get("meta", {})
+
+
+def _f32(inst):
+    inst.start = inst.start.astype(np.float32).astype(np.float64)
+    inst.goal = inst.goal.astype(np.float32).astype(np.float64)
+    return inst
+
+
+def generate_dataset(torch, insts, n_max: int, params: Params, max_iters: int = 3, chunk: int = 1024,
+                     pos_scale: float = 5.0, log=print):
+    """Plain batched solves of every instance (max_iters iterations); each
+    team's final plan is a training target.  Returns X [S][n_max][16],
+    M [S][n_max], Y [S][n_max][T*d_u] and the number of plans that already
+    met the goal tolerance."""
+    T, d_u = insts[0].T, insts[0].dims[1]
+    X, M, Y = [], [], []
+    solved = 0
+    t0 = time.time()
+    for c0 in range(0, len(insts), chunk):
+        part = insts[c0:c0 + chunk]
+        probs = [Problem(_f32(i)) for i in part]
+        p = Params(**{**params.__dict__, "instance_tag": (params.instance_tag + c0) % (1 << 19)})
+        outs = [torch.zeros((i.T, i.n, d_u), device="cuda") for i in part]
+        batch = d4orm_batch_create([pr.handle for pr in probs], p)
+        res = d4orm_batch_solve(batch, Budget(max_iters=max_iters), outs)
+        d4orm_batch_destroy(batch)
+        for inst, pr, o, r in zip(part, probs, outs, res):
+            solved += int(r["first_success_iter"] >= 0)
+            x, m = d4orm_warmstart_features(pr.handle, n_max, pos_scale)
+            y = np.zeros((n_max, T * d_u), dtype=np.float32)
+            y[:inst.n] = o.cpu().numpy().transpose(1, 0, 2).reshape(inst.n, T * d_u)
+            X.append(x)
+            M.append(m)
+            Y.append(y)
+        for pr in probs:
+            pr.close()
+        log(f"datagen {c0 + len(part)}/{len(insts)} within tolerance {solved} ({time.time() - t0:.0f} s)")
+    return np.stack(X), np.stack(M), np.stack(Y), solved
+
+
+def train(torch, X, M, Y, desc: WarmStartDesc, steps: int, batch: int, seed: int = 0, log=print):
+    ws = d4orm_warmstart_create(desc)
+    Xd, Md, Yd = (torch.as_tensor(a, device="cuda") for a in (X, M, Y))
+    rng = np.random.default_rng(seed)
+    idx = torch.zeros(batch, dtype=torch.int32, device="cuda")
+    curve = []
+    t0 = time.time()
+    for s in range(steps):
+        idx.copy_(torch.as_tensor(rng.integers(0, len(X), size=batch), dtype=torch.int32))
+        want = (s % 100 == 0) or s == steps - 1
+        loss = d4orm_warmstart_train_step(ws, Xd, Md, Yd, batch, idx_dev=idx, want_loss=want)
+        if want:
+            curve.append((s, loss))
+            if s % 2000 == 0 or s == steps - 1:
+                log(f"train step {s} loss {loss:.5f} ({time.time() - t0:.0f} s)")
+    torch.cuda.synchronize()
+    return ws, curve, time.time() - t0
+
+
+def evaluate(torch, ws, insts, params: Params, start_step: int, max_iters: int, log=print):
+    """Plain vs warm-started solves of the same held-out teams, one problem
+    at a time on the whole GPU (time to plan), same noise.  Warm: the
+    network's seed enters iteration 0 at start_step; later iterations are
+    the plain method (fallback).  Each problem's two graph shapes are
+    captured by an untimed solve first.  Then both sets again through the
+    batched persistent solver (throughput)."""
+    from . import d4orm_solve
+    d_u = insts[0].dims[1]
+    rows = []
+    for b, inst in enumerate(insts):
+        pr = Problem(_f32(inst))
+        p = Params(**{**params.__dict__, "instance_tag": b})
+        u = torch.zeros((inst.T, inst.n, d_u), device="cuda")
+        seed = torch.zeros_like(u)
+        d4orm_warmstart_predict(ws, pr.handle, p, start_step, seed)
+        d4orm_solve(pr.handle, p, Budget(max_iters=1), u)                                   # capture graphs
+        d4orm_solve(pr.handle, p, Budget(max_iters=1, start_step=start_step), u, du_init_dev=seed)
+        rp = d4orm_solve(pr.handle, p, Budget(max_iters=max_iters, stop_on_success=True), u)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d4orm_warmstart_predict(ws, pr.handle, p, start_step, seed)
+        predict_ms = (time.perf_counter() - t0) * 1e3
+        rw = d4orm_solve(pr.handle, p, Budget(max_iters=max_iters, stop_on_success=True, start_step=start_step), u,
+                         du_init_dev=seed)
+        rows.append(dict(n=inst.n, plain_ok=rp["first_success_iter"] >= 0, warm_ok=rw["first_success_iter"] >= 0,
+                         plain_ms=rp["ms_to_success"], warm_ms=rw["ms_to_success"] + predict_ms,
+                         plain_reward=rp["verdict"]["reward"], warm_reward=rw["verdict"]["reward"],
+                         plain_first=rp["first_success_iter"], warm_first=rw["first_success_iter"],
+                         predict_ms=predict_ms))
+        pr.close()
+        if (b + 1) % 100 == 0:
+            log(f"evaluated {b + 1}/{len(insts)}")
+
+    def summary(sel):
+        out = dict(count=len(sel), plain_solved=sum(r["plain_ok"] for r in sel),
+                   warm_solved=sum(r["warm_ok"] for r in sel))
+        both = [r for r in sel if r["plain_ok"] and r["warm_ok"]]
+        if both:
+            pm = statistics.median(r["plain_ms"] for r in both)
+            wm = statistics.median(r["warm_ms"] for r in both)
+            out.update(both=len(both), median_ms_plain=pm, median_ms_warm=wm, speedup=pm / wm,
+                       median_reward_ratio=statistics.median(r["warm_reward"] / r["plain_reward"] for r in both
+                                                             if r["plain_reward"] != 0),
+                       judged_worse_rate=sum(r["warm_reward"] < r["plain_reward"] - 0.01 * abs(r["plain_reward"])
+                                             for r in both) / len(both))
+        warm_ok = [r for r in sel if r["warm_ok"]]
+        out["fallback_rate"] = sum(r["warm_first"] != 0 for r in sel) / max(1, len(sel))
+        if warm_ok:
+            out["solved_by_seed_iteration"] = sum(r["warm_first"] == 0 for r in warm_ok) / len(warm_ok)
+        out["median_predict_ms"] = statistics.median(r["predict_ms"] for r in sel) if sel else None
+        return out
+
+    res = dict(all=summary(rows), n16=summary([r for r in rows if r["n"] == 16]))
+    # throughput view: the same teams through the batched persistent solver
+    probs = [Problem(_f32(i)) for i in insts]
+    batch = d4orm_batch_create([pr.handle for pr in probs], params, autotune=True)
+    outs = [torch.zeros((i.T, i.n, d_u), device="cuda") for i in insts]
+    seeds = [torch.zeros_like(o) for o in outs]
+    for pr, sd in zip(probs, seeds):
+        d4orm_warmstart_predict(ws, pr.handle, params, start_step, sd)
+    t0 = time.perf_counter()
+    bp = d4orm_batch_solve(batch, Budget(max_iters=max_iters, stop_on_success=True), outs)
+    plain_wall = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    bw = d4orm_batch_solve(batch, Budget(max_iters=max_iters, stop_on_success=True, start_step=start_step), outs,
+                           du_init_devs=seeds)
+    warm_wall = time.perf_counter() - t0
+    d4orm_batch_destroy(batch)
+    for pr in probs:
+        pr.close()
+    res["batched"] = dict(plain_wall_s=plain_wall, warm_wall_s=warm_wall,
+                          plain_solved=sum(r["first_success_iter"] >= 0 for r in bp),
+                          warm_solved=sum(r["first_success_iter"] >= 0 for r in bw),
+                          plain_iters=sum(r["iters_run"] for r in bp), warm_iters=sum(r["iters_run"] for r in bw))
+    log(json.dumps(res))
+    return res, rows
+
+
+def main():
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=50000)
+    ap.add_argument("--held-out", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--datagen-samples", type=int, default=2048)
+    ap.add_argument("--datagen-iters", type=int, default=3)
+    ap.add_argument("--eval-iters", type=int, default=10)
+    ap.add_argument("--eval-samples", type=int, default=4096)
+    ap.add_argument("--start-step", type=int, default=30)
+    ap.add_argument("--out", default=".")
+    args = ap.parse_args()
+    os.makedirs(args.out, exist_ok=True)
+    log_f = open(os.path.join(args.out, "warmstart_log.txt"), "w")
+
+    def log(msg):
+        print(msg, flush=True)
+        log_f.write(msg + "\n")
+        log_f.flush()
+
+    torch.cuda.set_device(0)
+    train_insts = scenarios_set(args.train, seed=3)
+    Xs, Ms, Ys, solved = generate_dataset(torch, train_insts, 16,
+                                          Params(n_samples=args.datagen_samples, n_steps=100, seed=3),
+                                          max_iters=args.datagen_iters, log=log)
+    log(f"dataset: {len(Xs)} plans ({solved} within the goal tolerance)")
+    desc = WarmStartDesc(n_max=16, T=80, d_u=2, width=256, max_batch=args.batch, seed=0, lr=1e-3,
+                         weight_decay=1e-4, pos_scale=5.0)
+    ws, curve, train_s = train(torch, Xs, Ms, Ys, desc, args.steps, args.batch, log=log)
+    params_np = d4orm_warmstart_get_params(ws)
+    save_weights(os.path.join(args.out, "setmlp_holo2d_T80.bin"), desc, params_np,
+                 meta=dict(train_instances=args.train, solved=int(solved), steps=args.steps,
+                           final_loss=curve[-1][1], train_seconds=train_s))
+    held = scenarios_set(args.held_out, seed=4)
+    res, rows = evaluate(torch, ws, held, Params(n_samples=args.eval_samples, n_steps=100, seed=4, instance_tag=0),
+                         args.start_step, args.eval_iters, log=log)
+    with open(os.path.join(args.out, "warmstart_rows.json"), "w") as f:
+        json.dump(rows, f)
+    res.update(dataset=int(solved), train_steps=args.steps, train_seconds=train_s, loss_curve=curve[::10])
+    with open(os.path.join(args.out, "warmstart_eval.json"), "w") as f:
+        json.dump(res, f)
+
+
+def scenarios_set(count, seed):
+    import scenarios
+    return scenarios.warmstart_set(count, seed)
+
+
+if __name__ == "__main__":
+    main()

@@ -91,16 +91,18 @@ def fibonacci_sphere(n: int, r: float) -> np.ndarray:
 def box_points(rng: np.random.Generator, n: int, d_p: int, half: float, min_sep: float) -> np.ndarray:
     """n points uniform in [-half, half]^d_p, pairwise >= min_sep apart
     (rejection sampling, one point at a time)."""
-    pts = []
+    pts = np.zeros((n, d_p))
+    placed = 0
     tries = 0
-    while len(pts) < n:
+    while placed < n:
         tries += 1
         if tries > 200000:
             raise RuntimeError("box_points: could not place points")
-        p = rng.uniform(-half, half, size=d_p)
-        if all(np.linalg.norm(p - q) >= min_sep for q in pts):
-            pts.append(p)
-    return np.array(pts)
+        q = rng.uniform(-half, half, size=d_p)
+        if placed == 0 or np.min(np.linalg.norm(pts[:placed] - q, axis=1)) >= min_sep:
+            pts[placed] = q
+            placed += 1
+    return pts
 
 
 # ---------------------------------------------------------------------------
@@ -172,6 +174,48 @@ def mixed_batch(count: int = 512, seed: int = 2, N: int = 1024) -> list[Instance
         u = rng.uniform()
         dyn = HOLO2D if u < 0.4 else (HOLO3D if u < 0.7 else UNICYCLE)
         out.append(box_instance(rng, dyn, n, T, N, tag=b, seed=0))
+    return out
+
+
+def reachable_box_instance(rng: np.random.Generator, n: int, T: int, N: int, *, side: float = 10.0,
+                           min_sep: float = 0.6, max_axis: float = 6.0, K: int = 100, iters: int = 5,
+                           tag: int = 0, seed: int = 0) -> Instance:
+    """2D holonomic team: starts uniform in a side x side box (>= min_sep
+    apart); each robot's goal uniform in the part of the box within max_axis
+    metres of its start along each axis (goals also >= min_sep apart), so
+    that every goal is reachable within T steps at |v|, |a| <= 1 with room
+    for detours (a 10 m box allows displacements the horizon cannot cover)."""
+    half = side / 2
+    p = box_points(rng, n, 2, half, min_sep)
+    gp = np.zeros_like(p)
+    for k in range(n):
+        lo = np.maximum(-half, p[k] - max_axis)
+        hi = np.minimum(half, p[k] + max_axis)
+        for _ in range(100000):
+            q = rng.uniform(lo, hi)
+            if k == 0 or np.min(np.linalg.norm(gp[:k] - q, axis=1)) >= min_sep:
+                gp[k] = q
+                break
+        else:
+            raise RuntimeError("reachable_box_instance: could not place a goal")
+    s, g = _full_state(HOLO2D, p, gp)
+    dd = _DYN_DEFAULTS[HOLO2D]
+    return Instance(f"reach_holo2d_n{n}_T{T}", HOLO2D, RK4, n, T, 0.1, dd["radius"], dd["u_lo"], dd["u_hi"],
+                    dd["v_max"], s, g, N=N, K=K, iters=iters, seed=seed, tag=tag)
+
+
+def warmstart_set(count: int, seed: int, N: int = 4096, T: int = 80, n_lo: int = 8, n_hi: int = 16,
+                  max_axis: float = 4.0, goal_tol: float = 0.5) -> list[Instance]:
+    """Teams of n ~ U{n_lo..n_hi} 2D holonomic robots for the learned warm
+    start (training and held-out sets use disjoint seeds); goals within
+    max_axis metres per axis of their starts; a plan reaches its goals when
+    every robot ends within goal_tol."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        inst = reachable_box_instance(rng, int(rng.integers(n_lo, n_hi + 1)), T, N, max_axis=max_axis)
+        inst.goal_tol = goal_tol
+        out.append(inst)
     return out
 
 

@@ -88,3 +88,21 @@ def test_null_arguments_rejected_without_gpu(g):
     assert lib.d4orm_denoise_step(None, None, 0, 1, None, None, None, None, None) == 1
     assert lib.d4orm_solve(None, None, None, None, None, None, None) == 1
     assert lib.d4orm_philox4x32_10(None, 0, 0, 1, None, None) == 1
+
+
+def test_warmstart_features_match_oracle(g):
+    """The network's input features are host code of the library: checked
+    against the oracle's features on a random 3D and a 2D problem."""
+    from oracle import setmlp
+    import scenarios
+    rng = np.random.default_rng(0)
+    for dyn in (scenarios.HOLO2D, scenarios.HOLO3D, scenarios.UNICYCLE):
+        inst = scenarios.box_instance(rng, dyn, 7, 12, 16)
+        start = inst.start.astype(np.float32).astype(np.float64)
+        goal = inst.goal.astype(np.float32).astype(np.float64)
+        h = g.d4orm_problem_create(inst.n, inst.T, inst.dyn, inst.integ, inst.dt, inst.radius, start, goal)
+        x, m = g.d4orm_warmstart_features(h, 10, 5.0)
+        xo, mo = setmlp.features(start, goal, inst.dims[2], 10, 5.0)
+        np.testing.assert_allclose(x, xo, rtol=1e-6, atol=1e-7)
+        np.testing.assert_array_equal(m, mo)
+        g.d4orm_problem_destroy(h)
