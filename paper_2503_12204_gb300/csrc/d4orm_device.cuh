@@ -87,19 +87,34 @@ __device__ __forceinline__ U4 philox4x32_10(U4 c, const DevStep& S)
     return c;
 }
 
+// Square root on the special-function unit (relative error ~2^-23): used
+// for the Eq. (4) distance, which enters a sum checked to 1e-3.
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Box-Muller: u1 = ((a >> 8) + 1) 2^-24 in (0, 1], u2 = (b >> 8) 2^-24 in
 // [0, 1) (both exact in binary32); z0 = r cos(2 pi u2), z1 = r sin(2 pi u2),
-// r = sqrt(-2 ln u1).  Accurate library functions (logf, sqrtf,
-// sincospif) keep the result within a few ulp of the exact transform.
+// r = sqrt(-2 ln u1).  Evaluated on the special-function unit: r^2 =
+// -2 ln 2 log2(u1) (hardware log2, absolute error <= 2^-22 on [0.5, 2], 2 ulp
+// elsewhere), approximate square root, and sin/cos of the angle shifted to
+// [-pi, pi) (2 pi u2 - pi; hardware sin/cos, absolute error <= 2^-21.41
+// there), with the signs flipped back.  Resulting bound on each normal:
+// |dz| <= 1e-6 r + min(2e-7 / r, 6e-4) -- a few 1e-7 for typical r, and at
+// most 6e-4 in the rare draws with r below 1e-3 -- far inside the rollout
+// and update tolerances.
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, float& z1)
 {
     const float u1 = (float)((a >> 8) + 1u) * 0x1.0p-24f;
-    const float u2 = (float)(b >> 8) * 0x1.0p-24f;
-    const float r = sqrtf(-2.0f * logf(u1));
+    const float r = sqrt_approx(fmaxf(-1.3862943611198906f * __log2f(u1), 0.0f));
+    const float ang = ((float)(b >> 8) * 0x1.0p-24f - 0.5f) * 6.283185307179586f;
     float s, c;
-    sincospif(2.0f * u2, &s, &c);
-    z0 = r * c;
-    z1 = r * s;
+    __sincosf(ang, &s, &c);
+    z0 = -r * c;
+    z1 = -r * s;
 }
 
 // Four standard normals: elements 4q..4q+3 of robot k's stream of sample j.
@@ -125,15 +140,6 @@ __device__ __forceinline__ long long globaltimer_ns()
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return (long long)t;
-}
-
-// Square root on the special-function unit (relative error ~2^-23): used
-// for the Eq. (4) distance, which enters a sum checked to 1e-3.
-__device__ __forceinline__ float sqrt_approx(float x)
-{
-    float r;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
 }
 
 // sin/cos of an arbitrary heading: Cody-Waite reduction by 2*pi (Cody and

@@ -165,7 +165,7 @@ __device__ __forceinline__ void batched_dispatch_seg(const DevProblem& P, const 
 #undef D4_CASE
 }
 
-__global__ void __launch_bounds__(kBatchMaxThreads)
+__global__ void __launch_bounds__(kBatchMaxThreads, 2)
 k_batched_solve(const DevProblem* __restrict__ probs, const BatchInstance* __restrict__ insts,
                 const int* __restrict__ order, const float4* __restrict__ sched, const BatchConsts C, int* queue,
                 BatchResult* results)

@@ -3,7 +3,9 @@ the same seeded inputs and the same Philox noise.
 
 Tolerances (FP32 path vs FP64 oracle):
 * Philox words: bit-exact.
-* eps: |d| <= 2e-6 |eps| + 1e-9 (a few binary32 ulp of accurate log/sqrt/sincospi).
+* eps: |d| <= 1.2e-6 r + min(2.4e-7 / r, 7e-4) + 1e-7 with r the Box-Muller
+  radius of the element's pair -- the error bound of the special-function
+  unit's log2, sqrt and sin/cos that the kernels use (margins of 20 %).
 * rollout states: <= 1e-4 absolute (metres, m/s, rad).
 * per-sample fitness: |d| <= 1e-3 |r| + 1e-5, plus w/(nT) per fragile
   robot-timestep -- one whose Eq. (5) indicator sits within 2e-4 m of its
@@ -78,10 +80,20 @@ def test_sample_noise_matches_oracle(torch, g, oracle_lib, dyn, n, T):
     g.d4orm_sample_noise(prob.handle, p, it, i, j0, count, eps)
     torch.cuda.synchronize()
     got = host(eps)
+    d_u = inst.dims[1]
     for s in range(count):
         want = oracle_lib.noise_block(oracle_problem(oracle_lib, inst), op, it, i, j0 + s)
+        # Box-Muller radius of each element's pair (stream elements 4q+0/1 and 4q+2/3)
+        r = np.zeros_like(want)
+        for t in range(T):
+            for k in range(n):
+                for d in range(d_u):
+                    e = t * d_u + d
+                    other = oracle_lib.noise(op, it, i, j0 + s, k, e ^ 1)
+                    r[t, k, d] = np.hypot(want[t, k, d], other)
         err = np.abs(got[s] - want)
-        assert (err <= 2e-6 * np.abs(want) + 1e-9).all(), err.max()
+        tol = 1.2e-6 * r + np.minimum(2.4e-7 / np.maximum(r, 1e-30), 7e-4) + 1e-7
+        assert (err <= tol).all(), (err / tol).max()
 
 
 # ----------------------------------------------------------------------------- rollout
