@@ -45,7 +45,9 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="unicycle_n8", choices=sorted(scenarios.WORKLOADS) + ["mixed512"])
+    ap.add_argument("--workload", default="unicycle_n8",
+                    choices=sorted(scenarios.WORKLOADS) + ["mixed512", "warmstart"])
+    ap.add_argument("--teams", type=int, default=200, help="held-out teams for --workload warmstart")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -310,6 +312,42 @@ def run_batched(args, torch, g, world, rank):
     g.d4orm_batch_destroy(batch)
 
 
+def run_warmstart(args, torch, g, world, rank):
+    """Median time to a collision-free plan with every robot within 0.5 m of
+    its goal, learned warm start vs the plain method, on held-out random 2D
+    holonomic teams (n 8..16, T = 80, N = 4096), one problem at a time on
+    the whole GPU, with the network trained by paper_2503_12204_gb300.warmstart
+    (weights shipped in the package)."""
+    from paper_2503_12204_gb300 import warmstart as W
+    desc, params_np, meta = W.load_weights(os.path.join(ROOT, "paper_2503_12204_gb300", "weights",
+                                                        "setmlp_holo2d_T80.bin"))
+    desc.max_batch = 1
+    ws = g.d4orm_warmstart_create(desc)
+    g.d4orm_warmstart_set_params(ws, params_np)
+    teams = scenarios.warmstart_set(args.teams, seed=4)
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        res, rows = W.evaluate(torch, ws, teams, g.Params(n_samples=4096, n_steps=100, seed=4), 30, 5,
+                               log=lambda m: None)
+    g.d4orm_warmstart_destroy(ws)
+    a = res["all"]
+    line = {
+        "metric": "ms to collision-free, goal-reaching plan (median; learned warm start vs plain)",
+        "value": a.get("median_ms_warm"), "unit": "ms", "n_gpus": world, "steps": args.teams, "warmup": 1,
+        "ms_per_step": a.get("median_ms_warm"), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (set-MLP bf16)", "data": "synthetic",
+        "config": {"workload": "warmstart_holo2d_T80", "teams": args.teams, "robots": "8..16", "samples_N": 4096,
+                   "start_step": 30, "max_iterations": 5, "goal_tol_m": 0.5},
+        "plain_median_ms": a.get("median_ms_plain"), "speedup": a.get("speedup"),
+        "median_reward_ratio": a.get("median_reward_ratio"), "judged_worse_rate": a.get("judged_worse_rate"),
+        "fallback_rate": a.get("fallback_rate"), "solved": {"plain": a["plain_solved"], "warm": a["warm_solved"],
+                                                           "both": a.get("both", 0)},
+        "n16": res["n16"], "batched": res["batched"], "clocks": clocks.summary(),
+        "training": meta,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_ours(args):
     import torch
 
@@ -324,8 +362,8 @@ def run_ours(args):
     barrier(torch, world)
     import paper_2503_12204_gb300 as g
 
-    if args.workload == "mixed512":
-        run_batched(args, torch, g, world, rank)
+    if args.workload in ("mixed512", "warmstart"):
+        (run_batched if args.workload == "mixed512" else run_warmstart)(args, torch, g, world, rank)
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()

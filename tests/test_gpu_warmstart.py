@@ -150,3 +150,44 @@ def test_predict_seeds_scaled_plan(torch, g):
     want = math.sqrt(ab[30]) * y.cpu().numpy()[0, :6].reshape(6, 10, 2).transpose(1, 0, 2)
     np.testing.assert_allclose(seed.cpu().numpy(), want, rtol=2e-6, atol=1e-7)
     g.d4orm_warmstart_destroy(ws)
+
+
+def test_trained_network_beats_untrained_and_zero_seed(torch, g):
+    """Ablation: the shipped network (trained on the method's own plans)
+    against the same architecture untrained and against no seed at all.
+    Each held-out team runs one iteration from step 30 of 100 (the warm
+    start's budget); the trained seed ends with a clearly higher Eq. (3)
+    reward and the robots closer to their goals."""
+    import os
+    import scenarios
+    from paper_2503_12204_gb300 import warmstart as W
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    desc, trained, _ = W.load_weights(os.path.join(root, "paper_2503_12204_gb300", "weights", "setmlp_holo2d_T80.bin"))
+    desc.max_batch = 1
+    nets = {}
+    for name in ("trained", "untrained"):
+        ws = g.d4orm_warmstart_create(desc)
+        if name == "trained":
+            g.d4orm_warmstart_set_params(ws, trained)
+        nets[name] = ws
+    teams = scenarios.warmstart_set(24, seed=4)
+    params = g.Params(n_samples=1024, n_steps=100, seed=4)
+    reward = {k: [] for k in ("trained", "untrained", "zero")}
+    for b, inst in enumerate(teams):
+        inst = round_instance(inst)
+        prob = g.Problem(inst)
+        p = g.Params(**{**params.__dict__, "instance_tag": b})
+        u = torch.zeros((inst.T, inst.n, 2), device="cuda")
+        for name in reward:
+            seed = torch.zeros_like(u)
+            if name != "zero":
+                g.d4orm_warmstart_predict(nets[name], prob.handle, p, 30, seed)
+            r = g.d4orm_solve(prob.handle, p, g.Budget(max_iters=1, start_step=30), u, du_init_dev=seed)
+            reward[name].append(r["verdict"]["reward"])
+    for ws in nets.values():
+        g.d4orm_warmstart_destroy(ws)
+    mean = {k: float(np.mean(v)) for k, v in reward.items()}
+    assert mean["trained"] > mean["untrained"] + 0.05, mean
+    assert mean["trained"] > mean["zero"] + 0.05, mean
+    wins = sum(t > z for t, z in zip(reward["trained"], reward["zero"]))
+    assert wins >= 20, (wins, mean)
