@@ -15,9 +15,9 @@
 // time) run on the helpers while the recurrence advances.  Per-row sums
 // (one row = one sample at one time step) are reduced inside lane segments
 // in a fixed order and added per sample at the end, so the result is
-// deterministic.  The mean controls u_base + c dU are read through the
-// read-only cache; shared memory holds two chunks of controls and positions,
-// laid out time-major (rows padded) so that warp accesses are conflict-free.
+// deterministic.  Shared memory holds the mean controls u_base + c dU, two
+// chunks of controls and positions (time-major, rows padded, so that warp
+// accesses are conflict-free) and the per-row terms.
 #include <cmath>
 
 #include "d4orm_internal.h"
@@ -48,7 +48,8 @@ size_t pipe_smem_bytes(const DevProblem& P)
     const size_t u = 2ull * SPC * kPipeCT * P.n * D::DU;
     const size_t pos = 2ull * SPC * kPipeCT * PosStride<SEG, D::DP>::RS;
     const size_t rows = (size_t)SPC * P.T;
-    return (u + pos + rows) * sizeof(float);
+    const size_t mean = (size_t)P.T * P.n * D::DU;
+    return (u + pos + rows + mean) * sizeof(float);
 }
 
 template <int DYN, int SEG>
@@ -67,6 +68,7 @@ k_rollout_fitness_pipe(const DevProblem P, const DevStep S, const float* __restr
     float* sU = smem;                                   // [2][CT][SPC][n][DU]
     float* sPos = sU + 2 * SPC * CT * n * DU;           // [2][CT*SPC][RS]
     float* sRows = sPos + 2 * SPC * CT * RS;            // [SPC][T]
+    float* sM = sRows + SPC * T;                         // [T][n][DU] mean controls
     const int u_slot = SPC * CT * n * DU;
     const int pos_slot = SPC * CT * RS;
 
@@ -75,6 +77,8 @@ k_rollout_fitness_pipe(const DevProblem P, const DevStep S, const float* __restr
     const uint32_t c3 = iter_word(S, it_dev);
     const int nchunks = (T + CT - 1) / CT;
     const int rowM = n * DU;
+    for (int e = threadIdx.x; e < T * rowM; e += blockDim.x) sM[e] = fmaf(S.c, du_in[e], u_base[e]);
+    __syncthreads();
     const int quads_per_chunk = CT * DU / 4;
 
     // rollout-warp state (warp 0)
@@ -109,10 +113,8 @@ k_rollout_fitness_pipe(const DevProblem P, const DevStep S, const float* __restr
                         const int e = 4 * (int)q + r;          // element of robot k's stream
                         const int t = e / DU, d = e - t * DU;
                         if (t < T) {
-                            const int gi = t * rowM + k * DU + d;
-                            const float m = fmaf(S.c, __ldg(&du_in[gi]), __ldg(&u_base[gi]));
                             U[(((t - c * CT) * SPC + s) * n + k) * DU + d] =
-                                clampf(fmaf(S.sigma, z[r], m), P.u_lo[d], P.u_hi[d]);
+                                clampf(fmaf(S.sigma, z[r], sM[t * rowM + k * DU + d]), P.u_lo[d], P.u_hi[d]);
                         }
                     }
                 }
@@ -253,7 +255,8 @@ size_t rollout_fitness_pipe_smem(const DevProblem& P)
     const int spc = 32 / seg;
     const size_t u = 2ull * spc * kPipeCT * P.n * P.d_u;
     const size_t pos = 2ull * spc * kPipeCT * (seg * P.d_p + 1);
-    return (u + pos + (size_t)spc * P.T) * sizeof(float);
+    const size_t mean = (size_t)P.T * P.n * P.d_u;
+    return (u + pos + (size_t)spc * P.T + mean) * sizeof(float);
 }
 
 }  // namespace d4orm
