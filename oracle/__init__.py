@@ -65,6 +65,7 @@ class _Problem(ctypes.Structure):
         ("goal_tol", ctypes.c_double), ("v_max", ctypes.c_double),
         ("u_lo", ctypes.c_double * 3), ("u_hi", ctypes.c_double * 3),
         ("start", ctypes.POINTER(ctypes.c_double)), ("goal", ctypes.POINTER(ctypes.c_double)),
+        ("n_obs", ctypes.c_int), ("obstacles", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -142,6 +143,7 @@ class Problem:
     eps_margin: float = 0.05
     goal_tol: float = 0.1
     v_max: float = 0.0
+    obstacles: np.ndarray | None = None   # [m][4]: centre x, y, z, radius (Appendix)
     _c: _Problem = field(default=None, init=False, repr=False)
 
     @property
@@ -154,8 +156,13 @@ class Problem:
         self._goal = np.ascontiguousarray(self.goal, dtype=np.float64).reshape(self.n, d_x)
         lo = (ctypes.c_double * 3)(*(list(self.u_lo) + [0.0] * (3 - d_u)))
         hi = (ctypes.c_double * 3)(*(list(self.u_hi) + [0.0] * (3 - d_u)))
+        if self.obstacles is not None and len(self.obstacles):
+            self._obs = np.ascontiguousarray(self.obstacles, dtype=np.float64).reshape(-1, 4)
+            n_obs, obs = self._obs.shape[0], _dp(self._obs)
+        else:
+            n_obs, obs = 0, None
         self._c = _Problem(self.n, self.T, self.dyn, self.integ, self.dt, self.radius, self.eps_margin,
-                           self.goal_tol, self.v_max, lo, hi, _dp(self._start), _dp(self._goal))
+                           self.goal_tol, self.v_max, lo, hi, _dp(self._start), _dp(self._goal), n_obs, obs)
         return self._c
 
     @property

@@ -200,8 +200,12 @@ static double pos_dist(const double *a, const double *b, int d_p)
  *          least R_a, so that a goal placed on its start stays finite);
  * Eq. (5): r_safe = -1 if some other robot l has |p_k[t]-p_l[t]| <= 2R_a+eps,
  *          else 0 (an indicator, not a per-pair count).
+ * Appendix (obstacles): each state of robot k that lies within r_o + R_a +
+ *          eps of an obstacle's centre (any obstacle; the same margin eps
+ *          as between robots) adds a second binary penalty -w.
  * threshold_gap (optional) receives min over t>=1 and pairs of
- * | |p_k - p_l| - (2R_a + eps) |: how far the sample is from an r_safe flip. */
+ * | |p_k - p_l| - (2R_a + eps) | and over robots and obstacles of
+ * | |p_k - c_o| - (r_o + R_a + eps) |: how far the sample is from a flip. */
 double orc_reward(const orc_problem *p, double w_safe, const double *states,
                   double *threshold_gap)
 {
@@ -225,7 +229,16 @@ double orc_reward(const orc_problem *p, double w_safe, const double *states,
                 double g = fabs(dkl - thr);
                 if (g < gap) gap = g;
             }
-            total += r_goal + w_safe * r_safe;
+            double r_obs = 0.0;
+            for (int o = 0; o < p->n_obs; ++o) {
+                const double *ob = p->obstacles + (size_t)o * 4;
+                const double thr_o = ob[3] + p->radius + p->eps_margin;
+                double dko = pos_dist(pk, ob, d_p);
+                if (dko <= thr_o) r_obs = -1.0;
+                double g = fabs(dko - thr_o);
+                if (g < gap) gap = g;
+            }
+            total += r_goal + w_safe * r_safe + w_safe * r_obs;
         }
     }
     if (threshold_gap) *threshold_gap = gap;
@@ -233,10 +246,12 @@ double orc_reward(const orc_problem *p, double w_safe, const double *states,
 }
 
 /* Fragility of the Eq. (5) indicator, for comparing a binary32 evaluation
- * against this one: the number of robot-timesteps (t >= 1, k) at which some
- * other robot's distance lies within delta of 2R_a + eps.  Only those
- * indicators can differ between two evaluations whose pair distances agree
- * to within delta; each such flip moves Eq. (3) by w / (nT). */
+ * against this one: the number of robot-timestep indicators (t >= 1, k; the
+ * robot-pair indicator and the obstacle indicator counted separately) for
+ * which some distance lies within delta of its threshold (2R_a + eps, or
+ * r_o + R_a + eps).  Only those indicators can differ between two
+ * evaluations whose distances agree to within delta; each such flip moves
+ * Eq. (3) by w / (nT). */
 int orc_fragile(const orc_problem *p, const double *states, double delta)
 {
     int d_x, d_u, d_p;
@@ -253,12 +268,20 @@ int orc_fragile(const orc_problem *p, const double *states, double delta)
                 if (fabs(dkl - thr) < delta) fragile = 1;
             }
             count += fragile;
+            int fragile_o = 0;
+            for (int o = 0; o < p->n_obs; ++o) {
+                const double *ob = p->obstacles + (size_t)o * 4;
+                double dko = pos_dist(&states[((size_t)t * n + k) * d_x], ob, d_p);
+                if (fabs(dko - (ob[3] + p->radius + p->eps_margin)) < delta) fragile_o = 1;
+            }
+            count += fragile_o;
         }
     return count;
 }
 
 /* Eq. (1) conditions and the Eq. (2) objective on a rolled-out plan.
- *   safety:   |p_k[t] - p_l[t]| > 2 R_a for all t in 0..T, k != l
+ *   safety:   |p_k[t] - p_l[t]| > 2 R_a for all t in 0..T, k != l, and
+ *             |p_k[t] - c_o| > r_o + R_a for every obstacle o (Appendix)
  *   terminal: |p_k[T] - g_k| <= goal_tol for all k (positions only)
  *   objective: 1/(nT) sum_k sum_{t=1..T} Ind[|p_k[t] - g_k| <= goal_tol] */
 void orc_verdict_of(const orc_problem *p, double w_safe, const double *states,
@@ -284,7 +307,14 @@ void orc_verdict_of(const orc_problem *p, double w_safe, const double *states,
             if (t == T && !(dg <= p->goal_tol)) reached = 0;
         }
     }
-    out->collision_free = (min_d > 2.0 * p->radius) ? 1 : 0;
+    int clear = 1;
+    for (int t = 0; t <= T; ++t)
+        for (int k = 0; k < n; ++k)
+            for (int o = 0; o < p->n_obs; ++o) {
+                const double *ob = p->obstacles + (size_t)o * 4;
+                if (!(pos_dist(&states[((size_t)t * n + k) * d_x], ob, d_p) > ob[3] + p->radius)) clear = 0;
+            }
+    out->collision_free = (min_d > 2.0 * p->radius && clear) ? 1 : 0;
     out->goal_reached = reached;
     out->reward = orc_reward(p, w_safe, states, NULL);
     out->objective = at_goal / ((double)n * (double)T);

@@ -56,6 +56,9 @@ typedef struct {
     double u_lo[3], u_hi[3]; /* per-component control box              */
     const double *start;     /* [n][d_x]  S                            */
     const double *goal;      /* [n][d_x]  T (positions used)           */
+    int n_obs;               /* static spherical obstacles (Appendix)   */
+    const double *obstacles; /* [n_obs][4]: centre x, y, z (z unused in
+                                2D), radius r_o                         */
 } orc_problem;
 
 typedef struct {

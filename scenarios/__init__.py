@@ -49,6 +49,7 @@ class Instance:
     goal_tol: float = 0.1
     beta0: float = 1e-4
     beta1: float = 1e-2
+    obstacles: np.ndarray | None = None   # [m][4]: centre x, y, z, radius (Appendix)
     extra: dict = field(default_factory=dict)
 
     @property

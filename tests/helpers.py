@@ -25,13 +25,16 @@ def round_instance(inst: scenarios.Instance) -> scenarios.Instance:
         setattr(r, name, f32(getattr(inst, name)))
     r.u_lo = tuple(f32(v) for v in inst.u_lo)
     r.u_hi = tuple(f32(v) for v in inst.u_hi)
+    if inst.obstacles is not None:
+        r.obstacles = np.asarray(inst.obstacles).astype(np.float32).astype(np.float64)
     return r
 
 
 def oracle_problem(o, inst: scenarios.Instance):
     return o.Problem(n=inst.n, T=inst.T, dyn=inst.dyn, integ=inst.integ, dt=inst.dt, radius=inst.radius,
                      start=inst.start, goal=inst.goal, u_lo=inst.u_lo, u_hi=inst.u_hi,
-                     eps_margin=inst.eps_margin, goal_tol=inst.goal_tol, v_max=inst.v_max)
+                     eps_margin=inst.eps_margin, goal_tol=inst.goal_tol, v_max=inst.v_max,
+                     obstacles=inst.obstacles)
 
 
 def oracle_params(o, inst: scenarios.Instance, N: int | None = None):
