@@ -56,6 +56,8 @@ def parse():
 def f32_inst(inst):
     inst.start = inst.start.astype(np.float32).astype(np.float64)
     inst.goal = inst.goal.astype(np.float32).astype(np.float64)
+    if inst.obstacles is not None:
+        inst.obstacles = np.asarray(inst.obstacles).astype(np.float32).astype(np.float64)
     return inst
 
 
@@ -66,7 +68,8 @@ def f32_inst(inst):
 #                       Box-Muller per normal: 5;
 #                       dynamics step: holonomic 8 d_p, unicycle 31, diff-drive 37;
 #                       goal term of Eq. (4) + accumulation: 3 d_p + 4;
-#   per unordered robot pair and timestep (Eq. (5)): 3 d_p + 1.
+#   per unordered robot pair and timestep (Eq. (5)): 3 d_p + 1;
+#   per robot, obstacle and timestep (obstacle penalty): 3 d_p + 1.
 # ---------------------------------------------------------------------------
 DYN_FLOPS = {scenarios.HOLO2D: 16, scenarios.HOLO3D: 24, scenarios.UNICYCLE: 31, scenarios.DIFFDRIVE4: 37}
 
@@ -75,7 +78,8 @@ def flops_per_sample_rollout(inst) -> int:
     d_x, d_u, d_p = inst.dims
     per_robot = 4 * d_u + 5 * d_u + DYN_FLOPS[inst.dyn] + 3 * d_p + 4
     per_pair = 3 * d_p + 1
-    return inst.T * (inst.n * per_robot + inst.n * (inst.n - 1) // 2 * per_pair)
+    n_obs = 0 if inst.obstacles is None else len(inst.obstacles)
+    return inst.T * (inst.n * per_robot + inst.n * (inst.n - 1) // 2 * per_pair + inst.n * n_obs * (3 * d_p + 1))
 
 
 def fp32_peak_tflops(sm_count: int, clock_mhz: float) -> float:
@@ -174,7 +178,8 @@ def cpu_oracle_rate(inst, budget_s: float = 15.0, n_sample: int | None = None) -
     import oracle
     op = oracle.Problem(n=inst.n, T=inst.T, dyn=inst.dyn, integ=inst.integ, dt=inst.dt, radius=inst.radius,
                         start=inst.start, goal=inst.goal, u_lo=inst.u_lo, u_hi=inst.u_hi,
-                        eps_margin=inst.eps_margin, goal_tol=inst.goal_tol, v_max=inst.v_max)
+                        eps_margin=inst.eps_margin, goal_tol=inst.goal_tol, v_max=inst.v_max,
+                        obstacles=inst.obstacles)
     d_u = inst.dims[1]
     rng = np.random.default_rng(0)
     u_base = scenarios.random_controls(rng, inst, 0.5)
@@ -413,14 +418,15 @@ def run_ours(args):
         t0 = time.perf_counter()
         h = g.d4orm_problem_create(inst.n, inst.T, inst.dyn, inst.integ, inst.dt, inst.radius, start_h.numpy(),
                                    goal_h.numpy(), eps_margin=inst.eps_margin, goal_tol=inst.goal_tol,
-                                   v_max=inst.v_max, u_lo=inst.u_lo, u_hi=inst.u_hi)
+                                   v_max=inst.v_max, u_lo=inst.u_lo, u_hi=inst.u_hi, obstacles=inst.obstacles)
         r = g.d4orm_solve(h, params, budget, u_out, stream=stream)
         u_h.copy_(u_out, non_blocking=True)
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
         g.d4orm_problem_destroy(h)
     e2e = max_over_ranks(torch, world, statistics.median(e2e_ms))
-    h2d = 2 * inst.n * d_x * 4
+    n_obs = 0 if inst.obstacles is None else len(inst.obstacles)
+    h2d = 2 * inst.n * d_x * 4 + n_obs * 16
     d2h = inst.T * inst.n * d_u * 4 + 40  # plan + result struct
 
     # ---------------- per-kernel breakdown (same kernels, same launch shapes)
@@ -450,7 +456,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": inst.name, "dynamics": scenarios.DYN_NAMES[inst.dyn], "robots": inst.n,
                    "horizon_T": inst.T, "samples_N": inst.N, "denoise_steps": inst.K, "iterations": inst.iters,
-                   "sample_rollouts_per_step": rollouts_per_step, "parallelism": f"replicas{world}",
+                   "obstacles": n_obs, "sample_rollouts_per_step": rollouts_per_step, "parallelism": f"replicas{world}",
                    "l2": "flushed between timed steps (256 MB write)"},
         "e2e": {"value": rollouts_per_step * world / (e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e},

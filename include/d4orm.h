@@ -68,6 +68,7 @@ typedef enum {
 #define D4ORM_MAX_ITERS 4096        /* iteration index fits 12 counter bits    */
 #define D4ORM_MAX_TAG ((1u << 20) - 1)
 #define D4ORM_MAX_CTRL 49152        /* T * n * d_u (mean controls in shared memory) */
+#define D4ORM_MAX_OBSTACLES 16
 
 typedef struct d4orm_problem d4orm_problem;
 
@@ -90,6 +91,12 @@ typedef struct {
     const float *u_lo;          /* host [d_u] control box, copied; NULL = the
                                    model's default box                        */
     const float *u_hi;          /* host [d_u]                                 */
+    int n_obstacles;            /* 0..D4ORM_MAX_OBSTACLES static spherical
+                                   obstacles (Appendix): each robot-step
+                                   inside radius + R_a + eps costs w in
+                                   Eq. (3); safety needs > radius + R_a     */
+    const float *obstacles;     /* host [n_obstacles][4]: centre x, y, z
+                                   (z ignored in 2D), radius > 0; copied     */
 } d4orm_problem_desc;
 
 /* Denoising parameters (Algorithm 1, Sec. IV-B/C). */
@@ -116,7 +123,8 @@ typedef struct {
 
 /* Eq. (1)/(2) evaluation of one plan. */
 typedef struct {
-    int collision_free;         /* |p_k - p_l| > 2 R_a for all t in 0..T      */
+    int collision_free;         /* |p_k - p_l| > 2 R_a for all t in 0..T, and
+                                   clear of every obstacle (radius + R_a)   */
     int goal_reached;           /* |p_k[T] - goal_k| <= goal_tol for all k    */
     float reward;               /* Eq. (3)                                    */
     float objective;            /* Eq. (2): fraction of (k, t>=1) at goal     */
@@ -134,8 +142,9 @@ typedef struct {
 /* Create a problem (Sec. III).  Copies every host array; allocates no
  * device memory (device workspace is allocated on first compute call).
  * Errors: INVALID_ARG for null desc/out/start/goal, n/T/dt/radius out of
- * range, bad enums, u_lo > u_hi; UNSUPPORTED for n > 32 or
- * T * n * d_u > D4ORM_MAX_CTRL.  *out is NULL on error. */
+ * range, bad enums, u_lo > u_hi, obstacles with radius <= 0 or a null
+ * array; UNSUPPORTED for n > 32, T * n * d_u > D4ORM_MAX_CTRL or more than
+ * D4ORM_MAX_OBSTACLES obstacles.  *out is NULL on error. */
 d4orm_status d4orm_problem_create(const d4orm_problem_desc *desc, d4orm_problem **out);
 
 /* Frees the handle and its device workspace (synchronises the device work

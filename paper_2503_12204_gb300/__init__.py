@@ -62,6 +62,7 @@ class _Desc(ctypes.Structure):
         ("goal_tol", ctypes.c_float), ("v_max", ctypes.c_float),
         ("start", ctypes.POINTER(ctypes.c_float)), ("goal", ctypes.POINTER(ctypes.c_float)),
         ("u_lo", ctypes.POINTER(ctypes.c_float)), ("u_hi", ctypes.POINTER(ctypes.c_float)),
+        ("n_obstacles", ctypes.c_int), ("obstacles", ctypes.POINTER(ctypes.c_float)),
     ]
 
 
@@ -245,8 +246,9 @@ def _verdict(v: _Verdict) -> dict:
 
 def d4orm_problem_create(n_robots: int, T: int, dyn: int, integ: int, dt: float, radius: float, start, goal,
                          eps_margin: float = 0.05, goal_tol: float = 0.1, v_max: float = 0.0,
-                         u_lo=None, u_hi=None) -> ctypes.c_void_p:
-    """Create a problem handle; start/goal are host sequences of n*d_x floats."""
+                         u_lo=None, u_hi=None, obstacles=None) -> ctypes.c_void_p:
+    """Create a problem handle; start/goal are host sequences of n*d_x floats;
+    obstacles (optional) rows of (x, y, z, radius)."""
     d_x, d_u, _ = DIMS.get(dyn, (4, 2, 2))
     flat_s = [float(v) for v in _flatten(start)]
     flat_g = [float(v) for v in _flatten(goal)]
@@ -256,9 +258,13 @@ def d4orm_problem_create(n_robots: int, T: int, dyn: int, integ: int, dt: float,
         raise ValueError("start/goal must hold n_robots * d_x values")
     lo = _fbuf(u_lo, d_u) if u_lo is not None else None
     hi = _fbuf(u_hi, d_u) if u_hi is not None else None
+    obs_flat = [float(v) for v in _flatten(obstacles)] if obstacles is not None else []
+    n_obs = len(obs_flat) // 4
+    obs = (ctypes.c_float * max(1, len(obs_flat)))(*obs_flat)
     desc = _Desc(n_robots, T, dyn, integ, dt, radius, eps_margin, goal_tol, v_max, s, g,
                  ctypes.cast(lo, ctypes.POINTER(ctypes.c_float)) if lo is not None else None,
-                 ctypes.cast(hi, ctypes.POINTER(ctypes.c_float)) if hi is not None else None)
+                 ctypes.cast(hi, ctypes.POINTER(ctypes.c_float)) if hi is not None else None,
+                 n_obs, ctypes.cast(obs, ctypes.POINTER(ctypes.c_float)) if n_obs else None)
     h = ctypes.c_void_p()
     _check(lib.d4orm_problem_create(ctypes.byref(desc), ctypes.byref(h)))
     return h
@@ -500,7 +506,7 @@ class Problem:
         self.handle = d4orm_problem_create(inst.n, inst.T, inst.dyn, inst.integ, inst.dt, inst.radius,
                                            inst.start, inst.goal, eps_margin=inst.eps_margin,
                                            goal_tol=inst.goal_tol, v_max=inst.v_max, u_lo=inst.u_lo,
-                                           u_hi=inst.u_hi)
+                                           u_hi=inst.u_hi, obstacles=getattr(inst, "obstacles", None))
 
     def close(self):
         if self.handle:

@@ -37,6 +37,7 @@ struct d4orm_batch {
     BatchConsts C{};
     size_t smem = 0;
     int threads = 256, grid = 0;
+    bool obstacles = false;            // any problem has obstacles: the kernel variant with the penalty
     float tuned_ms[3] = {-1.f, -1.f, -1.f};
     // cached graph for one (max_iters, stop_on_success, start_step, warm) combination
     cudaGraphExec_t graph = nullptr;
@@ -69,7 +70,7 @@ void batch_free(d4orm_batch* B)
 // schedule (2 steps, 1 iteration), for the autotuner.
 d4orm_status pilot_ms(d4orm_batch* B, int threads, float* ms)
 {
-    const int occ = batched_ctas_per_sm(threads, B->smem);
+    const int occ = batched_ctas_per_sm(B->obstacles, threads, B->smem);
     if (occ <= 0) {
         *ms = -1.f;
         return D4ORM_OK;
@@ -89,8 +90,8 @@ d4orm_status pilot_ms(d4orm_batch* B, int threads, float* ms)
         e = cudaMemsetAsync(B->d_queue, 0, sizeof(int), st);
         if (e == cudaSuccess && rep == 1) e = cudaEventRecord(e0, st);
         if (e == cudaSuccess)
-            e = launch_batched(B->d_probs, B->d_insts, B->d_order, B->d_sched, P, B->d_queue, B->d_results, grid,
-                               threads, st);
+            e = launch_batched(B->obstacles, B->d_probs, B->d_insts, B->d_order, B->d_sched, P, B->d_queue,
+                               B->d_results, grid, threads, st);
         if (e == cudaSuccess && rep == 1) e = cudaEventRecord(e1, st);
     }
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -130,6 +131,7 @@ d4orm_status d4orm_batch_create(d4orm_problem* const* problems, int count, const
     for (int b = 0; b < count; ++b) {
         const DevProblem& P = dev_problem(problems[b]);
         B->h_probs.push_back(P);
+        B->obstacles = B->obstacles || P.n_obs > 0;
         const int nc = P.T * P.n * P.d_u;
         B->nctrl.push_back(nc);
         ctrl_cap = std::max(ctrl_cap, nc);
@@ -162,7 +164,7 @@ d4orm_status d4orm_batch_create(d4orm_problem* const* problems, int count, const
     };
     cudaError_t e = cudaGetDevice(&B->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&B->sms, cudaDevAttrMultiProcessorCount, B->device);
-    if (e == cudaSuccess) e = prepare_batched();
+    if (e == cudaSuccess) e = prepare_batched(B->obstacles);
     if (e == cudaSuccess) {
         // the single-problem path's kernel attributes are not needed here
         e = cudaMalloc(&B->d_probs, sizeof(DevProblem) * count);
@@ -227,10 +229,10 @@ d4orm_status d4orm_batch_create(d4orm_problem* const* problems, int count, const
             best = cand[c];
         }
     }
-    int occ = batched_ctas_per_sm(best, B->smem);
+    int occ = batched_ctas_per_sm(B->obstacles, best, B->smem);
     if (occ <= 0) {
         best = 128;
-        occ = batched_ctas_per_sm(best, B->smem);
+        occ = batched_ctas_per_sm(B->obstacles, best, B->smem);
     }
     if (occ <= 0) return fail_cleanup(set_error(D4ORM_ERR_UNSUPPORTED, "batched kernel cannot be resident"));
     B->threads = best;
@@ -300,8 +302,8 @@ d4orm_status d4orm_batch_solve(d4orm_batch* B, const d4orm_budget* budget, const
             e = cudaMemcpyAsync(B->d_insts, B->h_insts, sizeof(BatchInstance) * B->count, cudaMemcpyHostToDevice, cap);
         if (e == cudaSuccess) e = cudaMemsetAsync(B->d_queue, 0, sizeof(int), cap);
         if (e == cudaSuccess)
-            e = launch_batched(B->d_probs, B->d_insts, B->d_order, B->d_sched, C, B->d_queue, B->d_results, B->grid,
-                               B->threads, cap);
+            e = launch_batched(B->obstacles, B->d_probs, B->d_insts, B->d_order, B->d_sched, C, B->d_queue,
+                               B->d_results, B->grid, B->threads, cap);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(B->h_results, B->d_results, sizeof(BatchResult) * B->count, cudaMemcpyDeviceToHost,
                                 cap);

@@ -341,6 +341,15 @@ d4orm_status d4orm_problem_create(const d4orm_problem_desc* desc, d4orm_problem*
     for (int i = 0; i < desc->n_robots * d_x; ++i)
         if (!std::isfinite(desc->start[i]) || !std::isfinite(desc->goal[i]))
             return fail(D4ORM_ERR_INVALID_ARG, "start/goal must be finite");
+    if (desc->n_obstacles < 0) return fail(D4ORM_ERR_INVALID_ARG, "n_obstacles must be >= 0");
+    if (desc->n_obstacles > D4ORM_MAX_OBSTACLES)
+        return fail(D4ORM_ERR_UNSUPPORTED, "more than %d obstacles", D4ORM_MAX_OBSTACLES);
+    if (desc->n_obstacles > 0 && !desc->obstacles) return fail(D4ORM_ERR_INVALID_ARG, "obstacles is null");
+    for (int o = 0; o < desc->n_obstacles; ++o) {
+        for (int c = 0; c < 4; ++c)
+            if (!std::isfinite(desc->obstacles[o * 4 + c])) return fail(D4ORM_ERR_INVALID_ARG, "obstacle not finite");
+        if (!(desc->obstacles[o * 4 + 3] > 0.f)) return fail(D4ORM_ERR_INVALID_ARG, "obstacle radius must be > 0");
+    }
 
     d4orm_problem* P = new (std::nothrow) d4orm_problem();
     if (!P) return fail(D4ORM_ERR_OOM, "host allocation failed");
@@ -385,6 +394,14 @@ d4orm_status d4orm_problem_create(const d4orm_problem_desc* desc, d4orm_problem*
         d0 = std::sqrt(d0);
         if (d0 < desc->radius) d0 = desc->radius;
         D.inv_d0[k] = (float)(1.0 / d0);
+    }
+    D.n_obs = desc->n_obstacles;
+    for (int o = 0; o < desc->n_obstacles; ++o) {
+        for (int c = 0; c < 3; ++c) D.obs_c[o * 3 + c] = c < d_p ? desc->obstacles[o * 4 + c] : 0.0f;
+        const double r = desc->obstacles[o * 4 + 3];
+        const double pen = r + desc->radius + desc->eps_margin, safe = r + desc->radius;
+        D.obs_pen2[o] = (float)(pen * pen);
+        D.obs_safe2[o] = (float)(safe * safe);
     }
     *out = P;
     return D4ORM_OK;

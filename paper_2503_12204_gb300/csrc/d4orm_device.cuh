@@ -9,6 +9,7 @@
 namespace d4orm {
 
 constexpr int kMaxRobots = 32;
+constexpr int kMaxObstacles = 16;
 constexpr unsigned kFull = 0xffffffffu;
 
 enum Dyn : int { HOLO2D = 0, HOLO3D = 1, UNICYCLE = 2, DIFFDRIVE4 = 3 };
@@ -35,7 +36,48 @@ struct DevProblem {
     float start[kMaxRobots * 6];
     float goal[kMaxRobots * 3];   // goal positions
     float inv_d0[kMaxRobots];     // 1 / max(|p0 - g|, R_a)  (Eq. (4))
+    // spherical obstacles (Appendix): centres, penalty radius^2 (r_o + R_a + eps)^2,
+    // safety radius^2 (r_o + R_a)^2
+    int n_obs;
+    float obs_c[kMaxObstacles * 3];
+    float obs_pen2[kMaxObstacles];
+    float obs_safe2[kMaxObstacles];
 };
+
+// Appendix obstacle term: does the robot at position p lie within the
+// penalty radius of any obstacle?
+template <int DP>
+__device__ __forceinline__ bool obstacle_hit(const DevProblem& P, const float* p)
+{
+    bool h = false;
+    for (int o = 0; o < P.n_obs; ++o) {
+        float d2 = 0.0f;
+#pragma unroll
+        for (int d = 0; d < DP; ++d) {
+            const float e = p[d] - P.obs_c[o * 3 + d];
+            d2 = fmaf(e, e, d2);
+        }
+        h |= d2 <= P.obs_pen2[o];
+    }
+    return h;
+}
+
+// Smallest (d^2 - safety radius^2) over obstacles; > 0 means clear.
+template <int DP>
+__device__ __forceinline__ float obstacle_clearance(const DevProblem& P, const float* p)
+{
+    float m = INFINITY;
+    for (int o = 0; o < P.n_obs; ++o) {
+        float d2 = 0.0f;
+#pragma unroll
+        for (int d = 0; d < DP; ++d) {
+            const float e = p[d] - P.obs_c[o * 3 + d];
+            d2 = fmaf(e, e, d2);
+        }
+        m = fminf(m, d2 - P.obs_safe2[o]);
+    }
+    return m;
+}
 
 // Per-step constants of step i in iteration it.
 struct DevStep {

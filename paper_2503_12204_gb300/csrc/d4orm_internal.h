@@ -93,12 +93,20 @@ struct BatchResult {
     long long ns_total;       // device clock of the instance's solve
 };
 
+// `obstacles` selects the kernel variant with the obstacle penalty compiled
+// in (any problem of the batch has obstacles).
 size_t batched_smem_bytes(const BatchConsts& C);
-cudaError_t prepare_batched();
-int batched_ctas_per_sm(int threads, size_t smem);
-cudaError_t launch_batched(const DevProblem* probs, const BatchInstance* insts, const int* order,
+cudaError_t prepare_batched(bool obstacles);
+int batched_ctas_per_sm(bool obstacles, int threads, size_t smem);
+cudaError_t launch_batched(bool obstacles, const DevProblem* probs, const BatchInstance* insts, const int* order,
                            const float4* sched, const BatchConsts& C, int* queue, BatchResult* results, int grid,
                            int threads, cudaStream_t st);
+// the obstacle variant's own entry points (k_batched_obs.cu)
+cudaError_t prepare_batched_obs();
+int batched_ctas_per_sm_obs(int threads, size_t smem);
+cudaError_t launch_batched_obs(const DevProblem* probs, const BatchInstance* insts, const int* order,
+                               const float4* sched, const BatchConsts& C, int* queue, BatchResult* results, int grid,
+                               int threads, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Learned warm start: set-MLP kernels (k_setmlp.cu)

@@ -150,9 +150,11 @@ __device__ __forceinline__ void softmax_block(const float* __restrict__ fitness,
 // Eq. (3)-(5) fitness of sample j.  sM holds the mean controls
 // M[t][k][d] = u_base + c_i dU_i.  Returns the sample's fitness (already
 // divided by nT) on every lane of the segment.  Shared by the single-problem
-// kernel and the batched solver.
+// kernel and the batched solver.  OBS compiles in the obstacle penalty
+// (problems without obstacles run the variant without it: a runtime loop
+// in the unrolled time loop costs about 6 %).
 // ---------------------------------------------------------------------------
-template <int DYN, int SEG>
+template <int DYN, int SEG, bool OBS>
 __device__ __forceinline__ float sample_fitness_segment(const DevProblem& P, const DevStep& S,
                                                         const float* __restrict__ sM, uint32_t c3, int j)
 {
@@ -222,6 +224,9 @@ __device__ __forceinline__ float sample_fitness_segment(const DevProblem& P, con
                     }
                 }
                 if (robot) acc += (1.0f - sqrt_approx(dg2) * inv_d0) - (hit ? w_safe : 0.0f);
+                // Appendix: binary obstacle penalty with the same weight
+                if constexpr (OBS)
+                    if (robot && obstacle_hit<DP>(P, x)) acc -= w_safe;
             }
         }
     }
@@ -268,6 +273,7 @@ __device__ __forceinline__ void apply_rollout_verdict_warp(const DevProblem& P, 
     if (states && robot)
         for (int c = 0; c < DX; ++c) states[(size_t)k * DX + c] = x[c];
     float min_d2 = pair_min(INFINITY);
+    float obs_clear = robot ? obstacle_clearance<DP>(P, x) : INFINITY;
     float acc = 0.0f;
     int at_goal = 0;
     float dg2 = 0.0f;
@@ -305,7 +311,9 @@ __device__ __forceinline__ void apply_rollout_verdict_warp(const DevProblem& P, 
         }
         if (robot) {
             min_d2 = fminf(min_d2, m);
-            acc += (1.0f - sqrtf(dg2) * inv_d0) - (hit ? w_safe : 0.0f);
+            obs_clear = fminf(obs_clear, obstacle_clearance<DP>(P, x));
+            const bool obs = obstacle_hit<DP>(P, x);
+            acc += (1.0f - sqrtf(dg2) * inv_d0) - (hit ? w_safe : 0.0f) - (obs ? w_safe : 0.0f);
             at_goal += dg2 <= P.tol2 ? 1 : 0;
         }
     }
@@ -317,12 +325,13 @@ __device__ __forceinline__ void apply_rollout_verdict_warp(const DevProblem& P, 
         acc_s += __shfl_xor_sync(kFull, acc_s, off);
         goal_s += __shfl_xor_sync(kFull, goal_s, off);
         min_d2 = fminf(min_d2, __shfl_xor_sync(kFull, min_d2, off));
+        obs_clear = fminf(obs_clear, __shfl_xor_sync(kFull, obs_clear, off));
         reached &= __shfl_xor_sync(kFull, reached, off);
     }
     if (k == 0) {
         if (verdict) {
             d4orm_verdict v;
-            v.collision_free = (P.n < 2 || min_d2 > P.safe2) ? 1 : 0;
+            v.collision_free = ((P.n < 2 || min_d2 > P.safe2) && obs_clear > 0.0f) ? 1 : 0;
             v.goal_reached = reached;
             v.reward = acc_s * P.inv_nT;
             v.objective = (float)goal_s * P.inv_nT;

@@ -54,13 +54,15 @@ d4orm_status setup_device(int dev, DeviceSetup** out)
         if (e != cudaSuccess) return d4orm::set_cuda_error(e, "cudaDeviceGetAttribute");
         d4orm::DevProblem probe{};
         const int widths[] = {1, 2, 4, 8, 16, 32};
-        for (int dyn = d4orm::HOLO2D; dyn <= d4orm::DIFFDRIVE4; ++dyn)
-            for (int n : widths) {
-                probe.dyn = dyn;
-                probe.n = n;
-                e = d4orm::prepare_rollout_fitness(probe);
-                if (e != cudaSuccess) return d4orm::set_cuda_error(e, "cudaFuncSetAttribute");
-            }
+        for (int obs = 0; obs <= 1; ++obs)
+            for (int dyn = d4orm::HOLO2D; dyn <= d4orm::DIFFDRIVE4; ++dyn)
+                for (int n : widths) {
+                    probe.dyn = dyn;
+                    probe.n = n;
+                    probe.n_obs = obs;
+                    e = d4orm::prepare_rollout_fitness(probe);
+                    if (e != cudaSuccess) return d4orm::set_cuda_error(e, "cudaFuncSetAttribute");
+                }
         s.scratch = static_cast<float*>(ptr);
         s.sm_count = sms;
         s.done = true;

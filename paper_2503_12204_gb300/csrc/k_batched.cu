@@ -1,244 +1,31 @@
-// k_batched.cu -- K5, the batched persistent solver.
-//
-// Many independent problems of uneven robot count, horizon and dynamics are
-// solved by one persistent launch.  Each CTA pops problem indices from an
-// atomic work queue (ordered longest-first by the host) and runs the whole of
-// Algorithm 2 for that problem by itself: every denoising step (Algorithm 1
-// body: Eq. (12) samples, Eq. (1) rollouts, Eq. (3)-(5) fitness, Sec. IV-C
-// normalisation + Eq. (6) softmax, Eq. (13) update) and every iteration end
-// (apply, rollout, Eq. (1)/(2) verdict, stop on success), synchronising only
-// with __syncthreads.  CTAs never wait for one another, so there is no
-// inter-CTA spin and nothing to time out.
-//
-// Per step the CTA stages the mean controls in shared memory, evaluates all
-// N samples with the same lane-segment code as the single-problem kernel,
-// runs the block softmax with weight compaction, and forms the weighted
-// noise sum quad block by quad block (noise regenerated from the same
-// Philox counters), each quad's per-warp partials added in a fixed order.
-#include <cmath>
-
-#include "d4orm_internal.h"
-#include "d4orm_kernels.cuh"
+// k_batched.cu -- K5 host entry points and the obstacle-free instantiation
+// (the kernel itself is in k_batched.cuh; k_batched_obs.cu holds the
+// variant with the obstacle penalty).
+#include "k_batched.cuh"
 
 namespace d4orm {
-
-template <int DYN, int SEG>
-__device__ __noinline__ void batched_instance(const DevProblem& P, const BatchInstance& I, const BatchConsts& C,
-                                                 const float4* __restrict__ sched, int b, float* sM, float* sFit,
-                                                 float2* sList, float4* sRed, float* sh, int* scan, int* s_count,
-                                                 d4orm_verdict* s_verdict, BatchResult* results)
-{
-    constexpr int DU = DynDims<DYN>::DU;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    const int nctrl = P.T * P.n * DU;
-    const int N = C.N;
-    float* tau = I.tau_u;
-    float* du[2] = {I.du0, I.du1};
-    const long long t_start = globaltimer_ns();
-
-    for (int e = tid; e < nctrl; e += nt) tau[e] = 0.0f;
-    int first = -1, iters = 0;
-    long long t_success = -1;
-    d4orm_verdict last{};
-    for (int it = 0; it < C.max_iters; ++it) {
-        // dU_K = 0 (Sec. IV-D); a warm start enters the first iteration at
-        // start_step with the given deformation
-        const bool warm = (it == 0) && I.du_init != nullptr;
-        for (int e = tid; e < nctrl; e += nt) du[0][e] = warm ? I.du_init[e] : 0.0f;
-        __syncthreads();
-        int cur = 0;
-        const uint32_t c3 = (uint32_t)it | ((C.tag_base + (uint32_t)b) << 12);
-        for (int i = warm ? C.start_step : C.K; i >= 1; --i) {
-            DevStep S;
-#pragma unroll
-            for (int r = 0; r < 10; ++r) {
-                S.rk0[r] = C.rk0[r];
-                S.rk1[r] = C.rk1[r];
-            }
-            const float4 sc = sched[i];
-            S.c2_step = (uint32_t)i << 8;
-            S.c3_tag = 0;
-            S.it = it;
-            S.N = N;
-            S.c = sc.x;
-            S.sigma = sc.y;
-            S.g = sc.z;
-            S.w_safe = C.w_safe;
-            S.inv_lambda = C.inv_lambda;
-            // mean controls M = tau.u + c dU_i
-            for (int e = tid; e < nctrl; e += nt) sM[e] = fmaf(S.c, du[cur][e], tau[e]);
-            __syncthreads();
-            // fitness of all N samples, 32/SEG per warp per pass
-            constexpr int SPW = 32 / SEG;
-            for (int base = 0; base < N; base += nw * SPW) {
-                const int j = base + warp * SPW + lane / SEG;
-                const float f = sample_fitness_segment<DYN, SEG>(P, S, sM, c3, j);
-                if ((lane & (SEG - 1)) == 0 && j < N) sFit[j] = f;
-            }
-            __syncthreads();
-            // batch softmax + compaction (Sec. IV-C, Eq. (6))
-            if (N <= 8 * nt)
-                softmax_block<8>(sFit, N, S.inv_lambda, sList, s_count, nullptr, sh, scan);
-            else
-                softmax_block<0>(sFit, N, S.inv_lambda, sList, s_count, nullptr, sh, scan);
-            __syncthreads();
-            // weighted noise sum and Eq. (13) update, 32 quads at a time
-            const int n_list = *s_count;
-            const int nQ = P.n * P.Q;
-            const int len = P.T * DU;
-            for (int qb = 0; qb < nQ; qb += 32) {
-                const int gq = qb + lane;
-                const bool valid = gq < nQ;
-                const int k = valid ? gq / P.Q : 0;
-                const int q = valid ? gq - k * P.Q : 0;
-                float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-                for (int e = warp; e < n_list; e += nw) {
-                    const float2 wj = sList[e];
-                    float z[4];
-                    noise_quad(S, c3, (uint32_t)q, (uint32_t)__float_as_int(wj.y), (uint32_t)k, z);
-                    a.x = fmaf(wj.x, z[0], a.x);
-                    a.y = fmaf(wj.x, z[1], a.y);
-                    a.z = fmaf(wj.x, z[2], a.z);
-                    a.w = fmaf(wj.x, z[3], a.w);
-                }
-                sRed[warp * 32 + lane] = a;
-                __syncthreads();
-                if (warp == 0 && valid) {
-                    float4 s = sRed[lane];
-                    for (int r = 1; r < nw; ++r) {
-                        const float4 o = sRed[r * 32 + lane];
-                        s.x += o.x; s.y += o.y; s.z += o.z; s.w += o.w;
-                    }
-                    const float sv[4] = {s.x, s.y, s.z, s.w};
-#pragma unroll
-                    for (int r4 = 0; r4 < 4; ++r4) {
-                        const int e = 4 * q + r4;
-                        if (e < len) {
-                            const int t = e / DU, d = e - t * DU;
-                            const int idx = (t * P.n + k) * DU + d;
-                            du[cur ^ 1][idx] = S.g * fmaf(S.sigma, sv[r4], S.c * du[cur][idx]);
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-            cur ^= 1;
-        }
-        // iteration end: tau.u <- clip(tau.u + dU_0), rollout, verdict
-        if (warp == 0) apply_rollout_verdict_warp<DYN>(P, C.w_safe, tau, du[cur], tau, nullptr, s_verdict);
-        __syncthreads();
-        last = *s_verdict;
-        iters = it + 1;
-        if (first < 0 && last.collision_free && last.goal_reached) {
-            first = it;
-            t_success = globaltimer_ns();
-        }
-        __syncthreads();
-        if (C.stop_on_success && first >= 0) break;
-    }
-    for (int e = tid; e < nctrl; e += nt) I.u_out[e] = tau[e];
-    if (tid == 0) {
-        BatchResult r;
-        r.verdict = last;
-        r.iters_run = iters;
-        r.first_success_iter = first;
-        r.ns_to_success = t_success >= 0 ? t_success - t_start : -1;
-        r.ns_total = globaltimer_ns() - t_start;
-        results[b] = r;
-    }
-}
-
-template <int DYN>
-__device__ __forceinline__ void batched_dispatch_seg(const DevProblem& P, const BatchInstance& I,
-                                                     const BatchConsts& C, const float4* sched, int b, float* sM,
-                                                     float* sFit, float2* sList, float4* sRed, float* sh, int* scan,
-                                                     int* s_count, d4orm_verdict* s_verdict, BatchResult* results)
-{
-#define D4_CASE(SEGV) batched_instance<DYN, SEGV>(P, I, C, sched, b, sM, sFit, sList, sRed, sh, scan, s_count, \
-                                                  s_verdict, results)
-    if (P.n <= 2) D4_CASE(2);
-    else if (P.n <= 4) D4_CASE(4);
-    else if (P.n <= 8) D4_CASE(8);
-    else if (P.n <= 16) D4_CASE(16);
-    else D4_CASE(32);
-#undef D4_CASE
-}
-
-__global__ void __launch_bounds__(kBatchMaxThreads, 2)
-k_batched_solve(const DevProblem* __restrict__ probs, const BatchInstance* __restrict__ insts,
-                const int* __restrict__ order, const float4* __restrict__ sched, const BatchConsts C, int* queue,
-                BatchResult* results)
-{
-    __shared__ DevProblem sP;
-    __shared__ float sh[33];
-    __shared__ int scan[33];
-    __shared__ int s_pick, s_count;
-    __shared__ d4orm_verdict s_verdict;
-    extern __shared__ float4 dyn_smem[];
-    float* sM = reinterpret_cast<float*>(dyn_smem);                 // [C.ctrl_cap]
-    float* sFit = sM + C.ctrl_cap;                                  // [C.n_cap]
-    float2* sList = reinterpret_cast<float2*>(sFit + C.n_cap);      // [C.n_cap]
-    float4* sRed = reinterpret_cast<float4*>(sList + C.n_cap);      // [32 warps][32]
-    for (;;) {
-        if (threadIdx.x == 0) s_pick = atomicAdd(queue, 1);
-        __syncthreads();
-        const int pick = s_pick;
-        if (pick >= C.count) break;
-        const int b = order[pick];
-        const int* src = reinterpret_cast<const int*>(&probs[b]);
-        int* dst = reinterpret_cast<int*>(&sP);
-        for (int w = threadIdx.x; w < (int)(sizeof(DevProblem) / 4); w += blockDim.x) dst[w] = src[w];
-        __syncthreads();
-        const BatchInstance I = insts[b];
-        switch (sP.dyn) {
-        case HOLO2D:
-            batched_dispatch_seg<HOLO2D>(sP, I, C, sched, b, sM, sFit, sList, sRed, sh, scan, &s_count, &s_verdict,
-                                         results);
-            break;
-        case HOLO3D:
-            batched_dispatch_seg<HOLO3D>(sP, I, C, sched, b, sM, sFit, sList, sRed, sh, scan, &s_count, &s_verdict,
-                                         results);
-            break;
-        case UNICYCLE:
-            batched_dispatch_seg<UNICYCLE>(sP, I, C, sched, b, sM, sFit, sList, sRed, sh, scan, &s_count,
-                                           &s_verdict, results);
-            break;
-        default:
-            batched_dispatch_seg<DIFFDRIVE4>(sP, I, C, sched, b, sM, sFit, sList, sRed, sh, scan, &s_count,
-                                             &s_verdict, results);
-            break;
-        }
-        __syncthreads();
-    }
-}
 
 size_t batched_smem_bytes(const BatchConsts& C)
 {
     return ((size_t)C.ctrl_cap + C.n_cap + 2ull * C.n_cap) * sizeof(float) + 32ull * 32 * sizeof(float4);
 }
 
-cudaError_t prepare_batched()
+cudaError_t prepare_batched(bool obstacles)
 {
-    return cudaFuncSetAttribute(k_batched_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    return obstacles ? prepare_batched_obs() : BatchedOps<false>::prepare();
 }
 
-int batched_ctas_per_sm(int threads, size_t smem)
+int batched_ctas_per_sm(bool obstacles, int threads, size_t smem)
 {
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched_solve, threads, smem) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    return occ;
+    return obstacles ? batched_ctas_per_sm_obs(threads, smem) : BatchedOps<false>::ctas_per_sm(threads, smem);
 }
 
-cudaError_t launch_batched(const DevProblem* probs, const BatchInstance* insts, const int* order,
+cudaError_t launch_batched(bool obstacles, const DevProblem* probs, const BatchInstance* insts, const int* order,
                            const float4* sched, const BatchConsts& C, int* queue, BatchResult* results, int grid,
                            int threads, cudaStream_t st)
 {
-    k_batched_solve<<<grid, threads, batched_smem_bytes(C), st>>>(probs, insts, order, sched, C, queue, results);
-    return cudaGetLastError();
+    if (obstacles) return launch_batched_obs(probs, insts, order, sched, C, queue, results, grid, threads, st);
+    return BatchedOps<false>::launch(probs, insts, order, sched, C, queue, results, grid, threads, st);
 }
 
 }  // namespace d4orm

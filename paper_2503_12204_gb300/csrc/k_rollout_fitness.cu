@@ -27,7 +27,7 @@ namespace d4orm {
 
 constexpr int kK2Threads = 256;
 
-template <int DYN, int SEG>
+template <int DYN, int SEG, bool OBS>
 __global__ void __launch_bounds__(kK2Threads)
 k_rollout_fitness(const DevProblem P, const DevStep S, const float* __restrict__ u_base,
                   const float* __restrict__ du_in, float* __restrict__ fitness, const int* __restrict__ it_dev)
@@ -43,41 +43,47 @@ k_rollout_fitness(const DevProblem P, const DevStep S, const float* __restrict__
     const int lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int j = warp * SPW + lane / SEG;
-    const float f = sample_fitness_segment<DYN, SEG>(P, S, sM, iter_word(S, it_dev), j);
+    const float f = sample_fitness_segment<DYN, SEG, OBS>(P, S, sM, iter_word(S, it_dev), j);
     if ((lane & (SEG - 1)) == 0 && j < S.N) fitness[j] = f;
 }
 
 // Opt in to up to 200 KB of dynamic shared memory (mean controls of the
 // largest problems).  Called outside any stream capture.
-template <int DYN, int SEG>
+template <int DYN, int SEG, bool OBS>
 static cudaError_t prepare_k2()
 {
-    return cudaFuncSetAttribute(k_rollout_fitness<DYN, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_rollout_fitness<DYN, SEG, OBS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 200 * 1024);
 }
 
-template <int DYN>
+template <int DYN, bool OBS>
 static cudaError_t prepare_dyn(int n)
 {
-    if (n <= 1) return prepare_k2<DYN, 1>();
-    if (n <= 2) return prepare_k2<DYN, 2>();
-    if (n <= 4) return prepare_k2<DYN, 4>();
-    if (n <= 8) return prepare_k2<DYN, 8>();
-    if (n <= 16) return prepare_k2<DYN, 16>();
-    return prepare_k2<DYN, 32>();
+    if (n <= 1) return prepare_k2<DYN, 1, OBS>();
+    if (n <= 2) return prepare_k2<DYN, 2, OBS>();
+    if (n <= 4) return prepare_k2<DYN, 4, OBS>();
+    if (n <= 8) return prepare_k2<DYN, 8, OBS>();
+    if (n <= 16) return prepare_k2<DYN, 16, OBS>();
+    return prepare_k2<DYN, 32, OBS>();
+}
+
+template <bool OBS>
+static cudaError_t prepare_k2_variant(const DevProblem& P)
+{
+    switch (P.dyn) {
+    case HOLO2D: return prepare_dyn<HOLO2D, OBS>(P.n);
+    case HOLO3D: return prepare_dyn<HOLO3D, OBS>(P.n);
+    case UNICYCLE: return prepare_dyn<UNICYCLE, OBS>(P.n);
+    case DIFFDRIVE4: return prepare_dyn<DIFFDRIVE4, OBS>(P.n);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t prepare_rollout_fitness(const DevProblem& P)
 {
     const cudaError_t e = prepare_rollout_fitness_pipe(P);
     if (e != cudaSuccess) return e;
-    switch (P.dyn) {
-    case HOLO2D: return prepare_dyn<HOLO2D>(P.n);
-    case HOLO3D: return prepare_dyn<HOLO3D>(P.n);
-    case UNICYCLE: return prepare_dyn<UNICYCLE>(P.n);
-    case DIFFDRIVE4: return prepare_dyn<DIFFDRIVE4>(P.n);
-    default: return cudaErrorInvalidValue;
-    }
+    return P.n_obs > 0 ? prepare_k2_variant<true>(P) : prepare_k2_variant<false>(P);
 }
 
 // Warps per CTA: every sample is the same amount of work, so the launch
@@ -99,7 +105,7 @@ static int pick_warps_per_cta(int total_warps, int sm_count)
     return best_w;
 }
 
-template <int DYN, int SEG>
+template <int DYN, int SEG, bool OBS>
 static cudaError_t launch_k2(const DevProblem& P, const DevStep& S, const float* u_base, const float* du_in,
                              float* fitness, const int* it_dev, int sm_count, cudaStream_t st)
 {
@@ -108,20 +114,33 @@ static cudaError_t launch_k2(const DevProblem& P, const DevStep& S, const float*
     const int w = pick_warps_per_cta(total_warps, sm_count);
     const size_t smem = (size_t)P.T * P.n * DynDims<DYN>::DU * sizeof(float);
     const int grid = (total_warps + w - 1) / w;
-    k_rollout_fitness<DYN, SEG><<<grid, 32 * w, smem, st>>>(P, S, u_base, du_in, fitness, it_dev);
+    k_rollout_fitness<DYN, SEG, OBS><<<grid, 32 * w, smem, st>>>(P, S, u_base, du_in, fitness, it_dev);
     return cudaGetLastError();
 }
 
-template <int DYN>
+template <int DYN, bool OBS>
 static cudaError_t dispatch_seg(const DevProblem& P, const DevStep& S, const float* u_base, const float* du_in,
                                 float* fitness, const int* it_dev, int sms, cudaStream_t st)
 {
-    if (P.n <= 1) return launch_k2<DYN, 1>(P, S, u_base, du_in, fitness, it_dev, sms, st);
-    if (P.n <= 2) return launch_k2<DYN, 2>(P, S, u_base, du_in, fitness, it_dev, sms, st);
-    if (P.n <= 4) return launch_k2<DYN, 4>(P, S, u_base, du_in, fitness, it_dev, sms, st);
-    if (P.n <= 8) return launch_k2<DYN, 8>(P, S, u_base, du_in, fitness, it_dev, sms, st);
-    if (P.n <= 16) return launch_k2<DYN, 16>(P, S, u_base, du_in, fitness, it_dev, sms, st);
-    return launch_k2<DYN, 32>(P, S, u_base, du_in, fitness, it_dev, sms, st);
+    if (P.n <= 1) return launch_k2<DYN, 1, OBS>(P, S, u_base, du_in, fitness, it_dev, sms, st);
+    if (P.n <= 2) return launch_k2<DYN, 2, OBS>(P, S, u_base, du_in, fitness, it_dev, sms, st);
+    if (P.n <= 4) return launch_k2<DYN, 4, OBS>(P, S, u_base, du_in, fitness, it_dev, sms, st);
+    if (P.n <= 8) return launch_k2<DYN, 8, OBS>(P, S, u_base, du_in, fitness, it_dev, sms, st);
+    if (P.n <= 16) return launch_k2<DYN, 16, OBS>(P, S, u_base, du_in, fitness, it_dev, sms, st);
+    return launch_k2<DYN, 32, OBS>(P, S, u_base, du_in, fitness, it_dev, sms, st);
+}
+
+template <bool OBS>
+static cudaError_t dispatch_dyn(const DevProblem& P, const DevStep& S, const float* u_base, const float* du_in,
+                                float* fitness, const int* it_dev, int sms, cudaStream_t st)
+{
+    switch (P.dyn) {
+    case HOLO2D: return dispatch_seg<HOLO2D, OBS>(P, S, u_base, du_in, fitness, it_dev, sms, st);
+    case HOLO3D: return dispatch_seg<HOLO3D, OBS>(P, S, u_base, du_in, fitness, it_dev, sms, st);
+    case UNICYCLE: return dispatch_seg<UNICYCLE, OBS>(P, S, u_base, du_in, fitness, it_dev, sms, st);
+    case DIFFDRIVE4: return dispatch_seg<DIFFDRIVE4, OBS>(P, S, u_base, du_in, fitness, it_dev, sms, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 int resolve_rollout_kernel(const DevProblem& P, int N, int sm_count, int requested)
@@ -141,13 +160,8 @@ cudaError_t launch_rollout_fitness(const DevProblem& P, const DevStep& S, const 
 {
     if (resolve_rollout_kernel(P, S.N, sm_count, kernel) == D4ORM_ROLLOUT_PIPELINE)
         return launch_rollout_fitness_pipe(P, S, u_base, du_in, fitness, it_dev, st);
-    switch (P.dyn) {
-    case HOLO2D: return dispatch_seg<HOLO2D>(P, S, u_base, du_in, fitness, it_dev, sm_count, st);
-    case HOLO3D: return dispatch_seg<HOLO3D>(P, S, u_base, du_in, fitness, it_dev, sm_count, st);
-    case UNICYCLE: return dispatch_seg<UNICYCLE>(P, S, u_base, du_in, fitness, it_dev, sm_count, st);
-    case DIFFDRIVE4: return dispatch_seg<DIFFDRIVE4>(P, S, u_base, du_in, fitness, it_dev, sm_count, st);
-    default: return cudaErrorInvalidValue;
-    }
+    return P.n_obs > 0 ? dispatch_dyn<true>(P, S, u_base, du_in, fitness, it_dev, sm_count, st)
+                       : dispatch_dyn<false>(P, S, u_base, du_in, fitness, it_dev, sm_count, st);
 }
 
 }  // namespace d4orm

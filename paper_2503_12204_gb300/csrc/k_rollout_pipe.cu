@@ -52,7 +52,7 @@ size_t pipe_smem_bytes(const DevProblem& P)
     return (u + pos + rows + mean) * sizeof(float);
 }
 
-template <int DYN, int SEG>
+template <int DYN, int SEG, bool OBS>
 __global__ void __launch_bounds__(PipeShape<SEG>::THREADS)
 k_rollout_fitness_pipe(const DevProblem P, const DevStep S, const float* __restrict__ u_base,
                        const float* __restrict__ du_in, float* __restrict__ fitness, const int* __restrict__ it_dev)
@@ -160,6 +160,9 @@ k_rollout_fitness_pipe(const DevProblem P, const DevStep S, const float* __restr
                             hit |= (l != k) & (l < n) & (d2 <= P.thr2);
                         }
                         term = (1.0f - sqrt_approx(dg2) * inv_d0) - (hit ? S.w_safe : 0.0f);
+                        // Appendix: binary obstacle penalty with the same weight
+                        if constexpr (OBS)
+                            if (obstacle_hit<DP>(P, p)) term -= S.w_safe;
                     }
                     term = seg_sum<SEG>(term);
                     if (k == 0 && row < rows && t < T) sRows[s * T + t] = term;
@@ -194,48 +197,62 @@ k_rollout_fitness_pipe(const DevProblem P, const DevStep S, const float* __restr
     }
 }
 
-template <int DYN, int SEG>
+template <int DYN, int SEG, bool OBS>
 static cudaError_t prepare_pipe()
 {
-    return cudaFuncSetAttribute(k_rollout_fitness_pipe<DYN, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_rollout_fitness_pipe<DYN, SEG, OBS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 200 * 1024);
 }
 
-template <int DYN, int SEG>
+template <int DYN, int SEG, bool OBS>
 static cudaError_t launch_pipe(const DevProblem& P, const DevStep& S, const float* u_base, const float* du_in,
                                float* fitness, const int* it_dev, cudaStream_t st)
 {
     constexpr int SPC = PipeShape<SEG>::SPC;
     const int grid = (S.N + SPC - 1) / SPC;
-    k_rollout_fitness_pipe<DYN, SEG><<<grid, PipeShape<SEG>::THREADS, pipe_smem_bytes<DYN, SEG>(P), st>>>(
+    k_rollout_fitness_pipe<DYN, SEG, OBS><<<grid, PipeShape<SEG>::THREADS, pipe_smem_bytes<DYN, SEG>(P), st>>>(
         P, S, u_base, du_in, fitness, it_dev);
     return cudaGetLastError();
 }
 
-template <int DYN>
-static cudaError_t pipe_seg(const DevProblem& P, const DevStep* S, const float* u_base, const float* du_in,
+template <int DYN, int SEG, bool OBS>
+static cudaError_t pipe_one(const DevProblem& P, const DevStep* S, const float* u_base, const float* du_in,
                             float* fitness, const int* it_dev, cudaStream_t st)
 {
     // S == nullptr: set the kernel attributes only
-    if (P.n <= 1) return S ? launch_pipe<DYN, 1>(P, *S, u_base, du_in, fitness, it_dev, st) : prepare_pipe<DYN, 1>();
-    if (P.n <= 2) return S ? launch_pipe<DYN, 2>(P, *S, u_base, du_in, fitness, it_dev, st) : prepare_pipe<DYN, 2>();
-    if (P.n <= 4) return S ? launch_pipe<DYN, 4>(P, *S, u_base, du_in, fitness, it_dev, st) : prepare_pipe<DYN, 4>();
-    if (P.n <= 8) return S ? launch_pipe<DYN, 8>(P, *S, u_base, du_in, fitness, it_dev, st) : prepare_pipe<DYN, 8>();
-    if (P.n <= 16)
-        return S ? launch_pipe<DYN, 16>(P, *S, u_base, du_in, fitness, it_dev, st) : prepare_pipe<DYN, 16>();
-    return S ? launch_pipe<DYN, 32>(P, *S, u_base, du_in, fitness, it_dev, st) : prepare_pipe<DYN, 32>();
+    return S ? launch_pipe<DYN, SEG, OBS>(P, *S, u_base, du_in, fitness, it_dev, st) : prepare_pipe<DYN, SEG, OBS>();
+}
+
+template <int DYN, bool OBS>
+static cudaError_t pipe_seg(const DevProblem& P, const DevStep* S, const float* u_base, const float* du_in,
+                            float* fitness, const int* it_dev, cudaStream_t st)
+{
+    if (P.n <= 1) return pipe_one<DYN, 1, OBS>(P, S, u_base, du_in, fitness, it_dev, st);
+    if (P.n <= 2) return pipe_one<DYN, 2, OBS>(P, S, u_base, du_in, fitness, it_dev, st);
+    if (P.n <= 4) return pipe_one<DYN, 4, OBS>(P, S, u_base, du_in, fitness, it_dev, st);
+    if (P.n <= 8) return pipe_one<DYN, 8, OBS>(P, S, u_base, du_in, fitness, it_dev, st);
+    if (P.n <= 16) return pipe_one<DYN, 16, OBS>(P, S, u_base, du_in, fitness, it_dev, st);
+    return pipe_one<DYN, 32, OBS>(P, S, u_base, du_in, fitness, it_dev, st);
+}
+
+template <bool OBS>
+static cudaError_t pipe_dyn(const DevProblem& P, const DevStep* S, const float* u_base, const float* du_in,
+                            float* fitness, const int* it_dev, cudaStream_t st)
+{
+    switch (P.dyn) {
+    case HOLO2D: return pipe_seg<HOLO2D, OBS>(P, S, u_base, du_in, fitness, it_dev, st);
+    case HOLO3D: return pipe_seg<HOLO3D, OBS>(P, S, u_base, du_in, fitness, it_dev, st);
+    case UNICYCLE: return pipe_seg<UNICYCLE, OBS>(P, S, u_base, du_in, fitness, it_dev, st);
+    case DIFFDRIVE4: return pipe_seg<DIFFDRIVE4, OBS>(P, S, u_base, du_in, fitness, it_dev, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 static cudaError_t pipe_dispatch(const DevProblem& P, const DevStep* S, const float* u_base, const float* du_in,
                                  float* fitness, const int* it_dev, cudaStream_t st)
 {
-    switch (P.dyn) {
-    case HOLO2D: return pipe_seg<HOLO2D>(P, S, u_base, du_in, fitness, it_dev, st);
-    case HOLO3D: return pipe_seg<HOLO3D>(P, S, u_base, du_in, fitness, it_dev, st);
-    case UNICYCLE: return pipe_seg<UNICYCLE>(P, S, u_base, du_in, fitness, it_dev, st);
-    case DIFFDRIVE4: return pipe_seg<DIFFDRIVE4>(P, S, u_base, du_in, fitness, it_dev, st);
-    default: return cudaErrorInvalidValue;
-    }
+    return P.n_obs > 0 ? pipe_dyn<true>(P, S, u_base, du_in, fitness, it_dev, st)
+                       : pipe_dyn<false>(P, S, u_base, du_in, fitness, it_dev, st);
 }
 
 cudaError_t prepare_rollout_fitness_pipe(const DevProblem& P)

@@ -150,6 +150,28 @@ _DYN_DEFAULTS = {
 }
 
 
+def circle_obstacles_n16(n_obstacles: int = 4, N: int = 4096) -> Instance:
+    """16 2D holonomic robots on a circle of radius 4 m with antipodal goals
+    (Sec. V-A layout) and 1..4 static disc obstacles of radius 0.4 m across
+    the crossing region (Appendix, obstacle study: 16 robots, 1-4
+    obstacles, at most 50 iterations): one at the centre, the others on a
+    1.6 m circle at angles 2 pi o / (m - 1) + pi / 4.  RK4 dt 0.1, T = 100,
+    R_a 0.2 m, |a| <= 1, |v| <= 1, N samples, 100 steps, 50 iterations."""
+    if not 1 <= n_obstacles <= 16:
+        raise ValueError("n_obstacles must be in 1..16")
+    p = circle_antipodal(16, 4.0)
+    s, g = _full_state(HOLO2D, p, -p)
+    obs = [[0.0, 0.0, 0.0, 0.4]]
+    m = n_obstacles - 1
+    for o in range(m):
+        a = 2.0 * np.pi * o / m + np.pi / 4
+        obs.append([1.6 * np.cos(a), 1.6 * np.sin(a), 0.0, 0.4])
+    inst = Instance(f"obstacles{n_obstacles}_holo2d_n16_T100_N{N}", HOLO2D, RK4, 16, 100, 0.1, 0.2, (-1.0, -1.0),
+                    (1.0, 1.0), 1.0, s, g, N=N, K=100, iters=50, seed=0)
+    inst.obstacles = np.array(obs)
+    return inst
+
+
 def box_instance(rng: np.random.Generator, dyn: int, n: int, T: int, N: int, *, side: float = 10.0,
                  min_sep: float = 0.6, K: int = 100, iters: int = 5, tag: int = 0, seed: int = 0) -> Instance:
     """Random starts, then goals, uniform in a side x side box (cube in 3D),
@@ -239,4 +261,5 @@ WORKLOADS = {
     "holo2d_n4": holo2d_circle_n4,
     "unicycle_n8": unicycle_circle_n8,
     "holo3d_n16": holo3d_sphere_n16,
+    "obstacles4_n16": circle_obstacles_n16,
 }

@@ -65,3 +65,35 @@ def build_library() -> None:
     mod = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mod)
     mod.build()
+
+
+def add_obstacles(inst: scenarios.Instance, count: int, seed: int, r_lo: float = 0.2, r_hi: float = 0.6,
+                  reach: float = 0.8):
+    """Place `count` obstacles at points along random robots' straight
+    start-goal segments, a fraction U(reach / 4, reach) of the way (so that
+    many samples touch them: short horizons want a small reach), radius
+    U(r_lo, r_hi); returns a binary32-rounded copy of the instance."""
+    rng = np.random.default_rng(seed)
+    d_p = inst.dims[2]
+    obs = np.zeros((count, 4))
+    for o in range(count):
+        k = int(rng.integers(inst.n))
+        a = rng.uniform(reach / 4, reach)
+        obs[o, :d_p] = (1 - a) * inst.start[k, :d_p] + a * inst.goal[k, :d_p] + rng.normal(0, 0.2, d_p)
+        obs[o, 3] = rng.uniform(r_lo, r_hi)
+    r = copy.deepcopy(inst)
+    r.obstacles = obs
+    return round_instance(r)
+
+
+def obstacle_safety_gap(inst: scenarios.Instance, states: np.ndarray) -> float:
+    """min over t in 0..T, robots and obstacles of | |p - c| - (r_o + R_a) |:
+    how far a plan is from flipping the obstacle part of the safety verdict."""
+    if inst.obstacles is None or len(inst.obstacles) == 0:
+        return np.inf
+    d_p = inst.dims[2]
+    p = states[:, :, None, :d_p]                               # [T+1][n][1][d_p]
+    c = np.asarray(inst.obstacles)[None, None, :, :d_p]        # [1][1][m][d_p]
+    d = np.sqrt(((p - c) ** 2).sum(-1))
+    return float(np.abs(d - (np.asarray(inst.obstacles)[:, 3] + inst.radius)).min())
+

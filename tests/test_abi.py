@@ -57,6 +57,8 @@ def _desc_ok():
     (dict(T=0), 1), (dict(dt=0.0), 1), (dict(radius=-1.0), 1), (dict(dyn=7), 1), (dict(integ=3), 1),
     (dict(T=10000, n_robots=16, dyn=1, start=np.zeros(96), goal=np.zeros(96)), 2),
     (dict(start=np.full(8, np.nan)), 1),
+    (dict(obstacles=[[0.0, 0.0, 0.0, 0.0]]), 1), (dict(obstacles=[[np.nan, 0.0, 0.0, 1.0]]), 1),
+    (dict(obstacles=np.tile([0.0, 0.0, 0.0, 1.0], (17, 1))), 2),
 ])
 def test_problem_create_rejects(g, override, status):
     args = _desc_ok()
@@ -78,6 +80,10 @@ def test_problem_create_and_destroy_on_host(g):
     assert h.value
     g.d4orm_problem_destroy(h)
     g.d4orm_problem_destroy(None)
+    h = g.d4orm_problem_create(3, 12, 2, 1, 0.1, 0.2, np.zeros(9), np.ones(9),
+                               obstacles=np.tile([1.0, 2.0, 0.0, 0.5], (16, 1)))
+    assert h.value
+    g.d4orm_problem_destroy(h)
 
 
 def test_null_arguments_rejected_without_gpu(g):

@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import scenarios
-from helpers import gpu_params, oracle_problem, round_instance
+from helpers import add_obstacles, gpu_params, obstacle_safety_gap, oracle_problem, round_instance
 
 pytestmark = pytest.mark.gpu
 
@@ -74,6 +74,31 @@ def test_batched_matches_single_solves(torch, g, oracle_lib, autotune):
         fin = np.linalg.norm(st[-1, :, :inst.dims[2]] - inst.goal[:, :inst.dims[2]], axis=1)
         if np.all(np.abs(fin - inst.goal_tol) > DELTA):
             assert res[b]["verdict"]["goal_reached"] == vo["goal_reached"]
+    g.d4orm_batch_destroy(batch)
+
+
+def test_batched_with_obstacles_matches_single_solves(torch, g, oracle_lib):
+    """Ragged batch where every other problem carries 1..16 obstacles: the
+    persistent kernel evaluates the same obstacle term as the single path."""
+    insts = _mixed(8, seed=9, N=256, K=5)
+    insts = [add_obstacles(i, 1 + (3 * b) % 16, seed=b) if b % 2 == 0 else i for b, i in enumerate(insts)]
+    probs = [g.Problem(i) for i in insts]
+    params = g.Params(n_samples=256, n_steps=5, seed=11, instance_tag=7)
+    outs = [torch.zeros((i.T, i.n, i.dims[1]), device="cuda") for i in insts]
+    batch = g.d4orm_batch_create([p.handle for p in probs], params, autotune=False)
+    res = g.d4orm_batch_solve(batch, g.Budget(max_iters=2), outs)
+    torch.cuda.synchronize()
+    for b, (inst, p) in enumerate(zip(insts, probs)):
+        single = g.Params(n_samples=256, n_steps=5, seed=11, instance_tag=7 + b)
+        u = torch.zeros_like(outs[b])
+        r1 = g.d4orm_solve(p.handle, single, g.Budget(max_iters=2), u)
+        a, s = outs[b].cpu().numpy(), u.cpu().numpy()
+        scale = max(np.abs(s).max(), 1e-3)
+        assert np.abs(a - s).max() <= 1e-3 * scale, (b, np.abs(a - s).max(), scale)
+        st = oracle_lib.rollout(oracle_problem(oracle_lib, inst), a.astype(np.float64))
+        vo = oracle_lib.verdict(oracle_problem(oracle_lib, inst), inst.w_safe, st)
+        if abs(vo["min_pair_dist"] - 2 * inst.radius) > DELTA and obstacle_safety_gap(inst, st) > DELTA:
+            assert res[b]["verdict"]["collision_free"] == vo["collision_free"] == r1["verdict"]["collision_free"]
     g.d4orm_batch_destroy(batch)
 
 

@@ -16,13 +16,15 @@ Tolerances (FP32 path vs FP64 oracle):
   (stage isolation), and again on the oracle's own fitness when no sample is
   fragile.
 """
+import copy
 import math
 
 import numpy as np
 import pytest
 
 import scenarios
-from helpers import gpu_params, oracle_params, oracle_problem, round_instance, small_instance
+from helpers import (add_obstacles, gpu_params, obstacle_safety_gap, oracle_params, oracle_problem, round_instance,
+                     small_instance)
 
 pytestmark = pytest.mark.gpu
 
@@ -183,6 +185,74 @@ def test_denoise_step_parity(torch, g, oracle_lib, dyn, integ, n, T, N, it, i, k
     inst = small_instance(dyn, n, T, N, integ=integ, seed=7, K=20)
     r = _check_step(torch, g, oracle_lib, inst, it, i, kernel=kernel)
     assert r["n_fragile"] <= max(2, 0.02 * N)
+
+
+OBSTACLE_CASES = [
+    # dyn, integ, n, T, N, obstacles, reach (fraction of the start-goal segment)
+    (0, 1, 5, 40, 300, 3, 0.8),
+    (1, 1, 9, 23, 200, 16, 0.4),   # 3D, the maximum obstacle count
+    (2, 1, 8, 50, 257, 4, 0.8),
+    (3, 0, 3, 17, 64, 2, 0.1),     # diff-drive from rest barely leaves its start in 17 steps
+    (0, 1, 32, 12, 70, 12, 0.05),
+]
+
+
+@pytest.mark.parametrize("kernel", [1, 2], ids=["register", "pipeline"])
+@pytest.mark.parametrize("dyn,integ,n,T,N,m,reach", OBSTACLE_CASES)
+def test_denoise_step_parity_obstacles(torch, g, oracle_lib, dyn, integ, n, T, N, m, reach, kernel):
+    """Appendix obstacle term inside the fused rollout + fitness: the same
+    per-sample tolerance as without obstacles (fragile indicators now also
+    count obstacle distances near r_o + R_a + eps), and the obstacles must
+    change the fitness of a good share of the samples (not vacuous).
+    Robots cross obstacle boundaries far more often than they pass another
+    robot at exactly 2R + eps, so up to a quarter of the samples may carry a
+    fragile indicator; the rest are held to the strict tolerance."""
+    inst = add_obstacles(small_instance(dyn, n, T, N, integ=integ, seed=7, K=20), m, seed=n + T, reach=reach)
+    r = _check_step(torch, g, oracle_lib, inst, 1, 11, kernel=kernel)
+    assert r["n_fragile"] <= max(2, 0.25 * N)
+    free = copy.deepcopy(inst)
+    free.obstacles = None
+    f_free, _ = oracle_lib.sample_fitness(oracle_problem(oracle_lib, free), oracle_params(oracle_lib, free), 1, 11,
+                                          r["u_base"], r["du_in"], np.arange(N))
+    changed = np.abs(r["fit_g"] - f_free) > 0.5 * inst.w_safe / (n * T)
+    assert changed.mean() >= 0.2, changed.mean()
+
+
+@pytest.mark.parametrize("dyn,integ,n,T,m", [(0, 1, 6, 60, 5), (1, 1, 4, 40, 3), (2, 1, 8, 80, 8)])
+def test_rollout_verdict_obstacles(torch, g, oracle_lib, dyn, integ, n, T, m):
+    """Eq. (1) safety with obstacles on the rollout entry point: the GPU's
+    collision_free flag equals the oracle's away from both thresholds, and
+    the reward carries the obstacle penalty within the fragile allowance."""
+    inst = add_obstacles(small_instance(dyn, n, T, N=8, integ=integ), m, seed=3 * n)
+    op = oracle_problem(oracle_lib, inst)
+    prob = g.Problem(inst)
+    robust = 0
+    for trial in range(6):
+        rng = np.random.default_rng(100 * trial + n)
+        u = scenarios.random_controls(rng, inst, scale=1.2).astype(np.float32)
+        v = g.d4orm_rollout(prob.handle, gpu_params(g, inst), dev(torch, u))
+        want = oracle_lib.rollout(op, u.astype(np.float64))
+        vo = oracle_lib.verdict(op, inst.w_safe, want)
+        if (n < 2 or abs(vo["min_pair_dist"] - 2 * inst.radius) > DELTA) and obstacle_safety_gap(inst, want) > DELTA:
+            assert v["collision_free"] == vo["collision_free"]
+            robust += 1
+        frag = oracle_lib.fragile(op, want, DELTA)
+        assert abs(v["reward"] - vo["reward"]) <= 1e-3 * abs(vo["reward"]) + 1e-5 + frag * inst.w_safe / (n * T)
+    assert robust >= 3
+
+
+def test_verdict_unsafe_only_because_of_an_obstacle(torch, g):
+    """One robot holding still: clear of a distant obstacle it is safe;
+    with the obstacle's safety radius reaching its start it is not."""
+    start = np.array([[0.0, 0.0, 0.0, 0.0]])
+    inst = scenarios.Instance("still", 0, 1, 1, 10, 0.1, 0.2, (-1.0, -1.0), (1.0, 1.0), 1.0, start, start, N=8)
+    u = torch.zeros((10, 1, 2), device="cuda")
+    for centre, safe in (([3.0, 0.0, 0.0, 0.5], True), ([0.6, 0.0, 0.0, 0.5], False)):
+        inst.obstacles = np.array([centre])
+        prob = g.Problem(round_instance(inst))
+        v = g.d4orm_rollout(prob.handle, gpu_params(g, inst), u)
+        assert v["collision_free"] is safe
+        assert v["goal_reached"]
 
 
 @pytest.mark.parametrize("dyn,n,T,N", [(0, 4, 50, 256), (2, 8, 100, 700), (1, 16, 37, 300), (3, 32, 9, 40)])
