@@ -74,7 +74,11 @@ class _Params(ctypes.Structure):
         ("N", ctypes.c_int), ("K", ctypes.c_int), ("lam", ctypes.c_double),
         ("w_safe", ctypes.c_double), ("beta0", ctypes.c_double), ("beta1", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("tag", ctypes.c_uint32),
+        ("update_rule", ctypes.c_int), ("mppi_sigma", ctypes.c_double),
     ]
+
+
+DENOISE, MPPI = 0, 1
 
 
 class _Verdict(ctypes.Structure):
@@ -182,9 +186,12 @@ class Params:
     beta1: float = 1e-2
     seed: int = 0
     tag: int = 0
+    update_rule: int = 0       # DENOISE (Eq. (12)-(13)) or MPPI
+    mppi_sigma: float = 0.0    # MPPI exploration standard deviation
 
     def c(self) -> _Params:
-        return _Params(self.N, self.K, self.lam, self.w_safe, self.beta0, self.beta1, self.seed, self.tag)
+        return _Params(self.N, self.K, self.lam, self.w_safe, self.beta0, self.beta1, self.seed, self.tag,
+                       self.update_rule, self.mppi_sigma)
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:

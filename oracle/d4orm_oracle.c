@@ -348,16 +348,39 @@ void orc_weights(int N, const double *r, double lambda, double *w)
     for (int j = 0; j < N; ++j) w[j] /= Z;
 }
 
+/* Scales of step i: the sample mean factor, the sample standard deviation
+ * and the factor on the weighted mean.
+ *   ORC_DENOISE (Eq. (12)-(13)): 1/sqrt(abar_i), sqrt(1/abar_i - 1),
+ *                                sqrt(abar_{i-1}).
+ *   ORC_MPPI: the softmax update the paper contrasts with in Sec. IV
+ *             (Williams et al. 2018), with no noise schedule: samples
+ *             dU + sigma eps around the current deformation, and the new
+ *             deformation is their weighted mean: 1, sigma, 1. */
+static void step_scales(const orc_params *pp, const double *abar, int i, double *mean_scale, double *sd,
+                        double *g)
+{
+    if (pp->update_rule == ORC_MPPI) {
+        *mean_scale = 1.0;
+        *sd = pp->mppi_sigma;
+        *g = 1.0;
+    } else {
+        *mean_scale = 1.0 / sqrt(abar[i]);
+        *sd = sqrt(1.0 / abar[i] - 1.0);
+        *g = sqrt(abar[i - 1]);
+    }
+}
+
 /* Sample j of step i (Algorithm 1, sampling line; Eq. (12)):
  *   dU_j ~ N(dU_i / sqrt(abar_i), (1/abar_i - 1) I),
- * drawn as dU_i / sqrt(abar_i) + sqrt(1/abar_i - 1) * eps_j. */
+ * drawn as dU_i / sqrt(abar_i) + sqrt(1/abar_i - 1) * eps_j
+ * (MPPI: dU_i + sigma * eps_j). */
 static void make_sample(const orc_problem *p, const orc_params *pp, int it, int i, int j,
                         const double *abar, const double *du_in, double *sample)
 {
     int d_x, d_u, d_p;
     orc_dims(p->dyn, &d_x, &d_u, &d_p);
-    const double mean_scale = 1.0 / sqrt(abar[i]);
-    const double sd = sqrt(1.0 / abar[i] - 1.0);
+    double mean_scale, sd, g;
+    step_scales(pp, abar, i, &mean_scale, &sd, &g);
     for (int t = 0; t < p->T; ++t)
         for (int k = 0; k < p->n; ++k)
             for (int d = 0; d < d_u; ++d) {
@@ -395,7 +418,7 @@ void orc_sample_fitness(const orc_problem *p, const orc_params *pp, int it, int 
 
 /* Weighted mean and one-step denoise, Algorithm 1 / Eq. (12)-(13):
  *   dU_bar = sum_j w_j dU_j   (weights already normalised),
- *   dU_{i-1} = sqrt(abar_{i-1}) * dU_bar.
+ *   dU_{i-1} = sqrt(abar_{i-1}) * dU_bar   (MPPI: dU_bar itself).
  * The mean is taken over the sampled (unclipped) deformations. */
 void orc_weighted_update(const orc_problem *p, const orc_params *pp, int it, int i,
                          const double *du_in, const double *w, double *du_out)
@@ -412,7 +435,8 @@ void orc_weighted_update(const orc_problem *p, const orc_params *pp, int it, int
         make_sample(p, pp, it, i, j, abar, du_in, sample);
         for (size_t e = 0; e < nu; ++e) acc[e] += w[j] * sample[e];
     }
-    const double g = sqrt(abar[i - 1]);
+    double mean_scale, sd, g;
+    step_scales(pp, abar, i, &mean_scale, &sd, &g);
     for (size_t e = 0; e < nu; ++e) du_out[e] = g * acc[e];
     free(alpha); free(abar); free(sample); free(acc);
 }

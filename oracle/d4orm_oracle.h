@@ -69,7 +69,11 @@ typedef struct {
     double beta0, beta1;/* linear noise schedule end points           */
     uint64_t seed;      /* Philox key                                 */
     uint32_t tag;       /* instance tag (counter word)                */
+    int update_rule;    /* ORC_DENOISE (Eq. (12)-(13)) or ORC_MPPI    */
+    double mppi_sigma;  /* MPPI exploration standard deviation        */
 } orc_params;
+
+enum { ORC_DENOISE = 0, ORC_MPPI = 1 };
 
 typedef struct {
     int collision_free; /* Eq. (1) safety over states 0..T            */
