@@ -99,6 +99,17 @@ typedef struct {
                                    (z ignored in 2D), radius > 0; copied     */
 } d4orm_problem_desc;
 
+/* Update rules.  DENOISE is the method (Eq. (12)-(13)): samples
+ * dU_i / sqrt(abar_i) + sqrt(1/abar_i - 1) eps, new deformation
+ * sqrt(abar_{i-1}) * (weighted mean).  MPPI is the softmax update the paper
+ * contrasts its schedule with (Sec. IV-B; Williams et al.): samples
+ * dU + mppi_sigma * eps around the current deformation and the new
+ * deformation is their weighted mean, the same at every step (no
+ * schedule; beta0/beta1 unused).  Both use the same sampling, rollout,
+ * Eq. (3) fitness, Sec. IV-C normalisation and Eq. (6) weights. */
+#define D4ORM_UPDATE_DENOISE 0
+#define D4ORM_UPDATE_MPPI 1
+
 /* Denoising parameters (Algorithm 1, Sec. IV-B/C). */
 typedef struct {
     int n_samples;              /* N (the paper's M), >= 1                    */
@@ -108,6 +119,9 @@ typedef struct {
     float beta0, beta1;         /* linear noise schedule, 0 < beta < 1        */
     uint64_t seed;              /* Philox key                                 */
     uint32_t instance_tag;      /* <= D4ORM_MAX_TAG; separates instances      */
+    int update_rule;            /* D4ORM_UPDATE_DENOISE (0) or _MPPI (1)      */
+    float mppi_sigma;           /* MPPI sample standard deviation, > 0 when
+                                   update_rule is MPPI; unused otherwise     */
 } d4orm_params;
 
 /* Anytime budget of Algorithm 2. */

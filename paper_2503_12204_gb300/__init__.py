@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libd4orm.so")
 HOLO2D, HOLO3D, UNICYCLE, DIFFDRIVE4 = 0, 1, 2, 3
 EULER, RK4 = 0, 1
 ROLLOUT_AUTO, ROLLOUT_REGISTER, ROLLOUT_PIPELINE = 0, 1, 2
+UPDATE_DENOISE, UPDATE_MPPI = 0, 1
 DIMS = {HOLO2D: (4, 2, 2), HOLO3D: (6, 3, 3), UNICYCLE: (3, 2, 2), DIFFDRIVE4: (4, 2, 2)}
 MAX_ROBOTS = 32
 MAX_ITERS = 4096
@@ -71,6 +72,7 @@ class _Params(ctypes.Structure):
         ("n_samples", ctypes.c_int), ("n_steps", ctypes.c_int), ("temperature", ctypes.c_float),
         ("w_safe", ctypes.c_float), ("beta0", ctypes.c_float), ("beta1", ctypes.c_float),
         ("seed", ctypes.c_uint64), ("instance_tag", ctypes.c_uint32),
+        ("update_rule", ctypes.c_int), ("mppi_sigma", ctypes.c_float),
     ]
 
 
@@ -221,10 +223,12 @@ class Params:
     beta1: float = 1e-2
     seed: int = 0
     instance_tag: int = 0
+    update_rule: int = 0       # UPDATE_DENOISE or UPDATE_MPPI
+    mppi_sigma: float = 0.0
 
     def c(self) -> _Params:
         return _Params(self.n_samples, self.n_steps, self.temperature, self.w_safe, self.beta0, self.beta1,
-                       self.seed, self.instance_tag)
+                       self.seed, self.instance_tag, self.update_rule, self.mppi_sigma)
 
 
 @dataclass

@@ -172,6 +172,10 @@ d4orm_status check_params(const d4orm_problem* P, const d4orm_params* p)
     if (!(p->beta0 > 0.f && p->beta0 < 1.f && p->beta1 > 0.f && p->beta1 < 1.f))
         return fail(D4ORM_ERR_INVALID_ARG, "beta0/beta1 must lie in (0,1)");
     if (p->instance_tag > D4ORM_MAX_TAG) return fail(D4ORM_ERR_INVALID_ARG, "instance_tag too large");
+    if (p->update_rule != D4ORM_UPDATE_DENOISE && p->update_rule != D4ORM_UPDATE_MPPI)
+        return fail(D4ORM_ERR_INVALID_ARG, "unknown update_rule");
+    if (p->update_rule == D4ORM_UPDATE_MPPI && !(p->mppi_sigma > 0.f && std::isfinite(p->mppi_sigma)))
+        return fail(D4ORM_ERR_INVALID_ARG, "mppi_sigma must be > 0 and finite");
     (void)P;
     return D4ORM_OK;
 }
@@ -202,9 +206,16 @@ DevStep step_consts(const d4orm_params* p, const std::vector<double>& abar, int 
     S.c3_tag = p->instance_tag << 12;
     S.it = it;
     S.N = p->n_samples;
-    S.c = (float)(1.0 / std::sqrt(abar[i]));
-    S.sigma = (float)std::sqrt(1.0 / abar[i] - 1.0);
-    S.g = (float)std::sqrt(abar[i - 1]);
+    if (p->update_rule == D4ORM_UPDATE_MPPI) {
+        // no schedule: samples around the current deformation, new one = weighted mean
+        S.c = 1.0f;
+        S.sigma = p->mppi_sigma;
+        S.g = 1.0f;
+    } else {
+        S.c = (float)(1.0 / std::sqrt(abar[i]));
+        S.sigma = (float)std::sqrt(1.0 / abar[i] - 1.0);
+        S.g = (float)std::sqrt(abar[i - 1]);
+    }
     S.w_safe = p->w_safe;
     S.inv_lambda = (float)(1.0 / (double)p->temperature);
     return S;
@@ -227,7 +238,7 @@ bool same_params(const d4orm_params& a, const d4orm_params& b)
 {
     return a.n_samples == b.n_samples && a.n_steps == b.n_steps && a.temperature == b.temperature &&
            a.w_safe == b.w_safe && a.beta0 == b.beta0 && a.beta1 == b.beta1 && a.seed == b.seed &&
-           a.instance_tag == b.instance_tag;
+           a.instance_tag == b.instance_tag && a.update_rule == b.update_rule && a.mppi_sigma == b.mppi_sigma;
 }
 
 // Steps i0..1 of one iteration (ping-pong between d_du[0] -> ...), the

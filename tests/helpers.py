@@ -37,14 +37,16 @@ def oracle_problem(o, inst: scenarios.Instance):
                      obstacles=inst.obstacles)
 
 
-def oracle_params(o, inst: scenarios.Instance, N: int | None = None):
+def oracle_params(o, inst: scenarios.Instance, N: int | None = None, update=(0, 0.0)):
+    """update = (rule, mppi_sigma): rule 0 is the method, 1 is MPPI."""
     return o.Params(N=N or inst.N, K=inst.K, lam=inst.lam, w_safe=inst.w_safe, beta0=inst.beta0,
-                    beta1=inst.beta1, seed=inst.seed, tag=inst.tag)
+                    beta1=inst.beta1, seed=inst.seed, tag=inst.tag, update_rule=update[0], mppi_sigma=update[1])
 
 
-def gpu_params(g, inst: scenarios.Instance, N: int | None = None):
+def gpu_params(g, inst: scenarios.Instance, N: int | None = None, update=(0, 0.0)):
     return g.Params(n_samples=N or inst.N, n_steps=inst.K, temperature=inst.lam, w_safe=inst.w_safe,
-                    beta0=inst.beta0, beta1=inst.beta1, seed=inst.seed, instance_tag=inst.tag)
+                    beta0=inst.beta0, beta1=inst.beta1, seed=inst.seed, instance_tag=inst.tag,
+                    update_rule=update[0], mppi_sigma=update[1])
 
 
 def small_instance(dyn: int, n: int, T: int, N: int, integ: int = scenarios.RK4, seed: int = 0,

@@ -102,6 +102,32 @@ def test_batched_with_obstacles_matches_single_solves(torch, g, oracle_lib):
     g.d4orm_batch_destroy(batch)
 
 
+def test_batched_mppi_matches_single_solves(torch, g):
+    """The MPPI rule through the batched solver's schedule table equals the
+    single-problem MPPI solve with the same tag.  MPPI keeps sigma = 0.4 at
+    every step (no shrinking schedule), so the reduction-order rounding of
+    the two paths is amplified by the lambda = 0.1 softmax more than under
+    the method's schedule: one iteration of 5 steps, 2e-3 of the plan's
+    scale (a wrong constant would differ by O(sigma))."""
+    insts = _mixed(6, seed=12, N=256, K=5)
+    probs = [g.Problem(i) for i in insts]
+    params = g.Params(n_samples=256, n_steps=5, seed=2, instance_tag=90, update_rule=g.UPDATE_MPPI, mppi_sigma=0.4)
+    outs = [torch.zeros((i.T, i.n, i.dims[1]), device="cuda") for i in insts]
+    batch = g.d4orm_batch_create([p.handle for p in probs], params, autotune=False)
+    res = g.d4orm_batch_solve(batch, g.Budget(max_iters=1), outs)
+    torch.cuda.synchronize()
+    for b, p in enumerate(probs):
+        single = g.Params(n_samples=256, n_steps=5, seed=2, instance_tag=90 + b, update_rule=g.UPDATE_MPPI,
+                          mppi_sigma=0.4)
+        u = torch.zeros_like(outs[b])
+        r1 = g.d4orm_solve(p.handle, single, g.Budget(max_iters=1), u)
+        a, s = outs[b].cpu().numpy(), u.cpu().numpy()
+        scale = max(np.abs(s).max(), 1e-3)
+        assert np.abs(a - s).max() <= 2e-3 * scale, (b, np.abs(a - s).max(), scale)
+        assert res[b]["verdict"]["goal_reached"] == r1["verdict"]["goal_reached"]
+    g.d4orm_batch_destroy(batch)
+
+
 def test_batched_stop_on_success_and_warm_start(torch, g):
     start = np.array([[-1.5, 0, 0, 0], [1.5, 0, 0, 0]])
     swap = round_instance(scenarios.Instance("swap", 0, 1, 2, 60, 0.1, 0.2, (-1.0, -1.0), (1.0, 1.0), 1.0, start,

@@ -130,7 +130,7 @@ def test_rollout_states_and_verdict(torch, g, oracle_lib, dyn, integ, n, T):
 
 # ----------------------------------------------------------------------------- one step
 
-def _check_step(torch, g, o, inst, it, i, max_oracle_samples=None, seed=0, kernel=0):
+def _check_step(torch, g, o, inst, it, i, max_oracle_samples=None, seed=0, kernel=0, update=(0, 0.0)):
     rng = np.random.default_rng(seed)
     d_u = inst.dims[1]
     u_base = scenarios.random_controls(rng, inst, scale=0.5).astype(np.float32)
@@ -139,7 +139,7 @@ def _check_step(torch, g, o, inst, it, i, max_oracle_samples=None, seed=0, kerne
     g.d4orm_problem_set_rollout_kernel(prob.handle, kernel)
     if kernel:
         assert g.d4orm_problem_rollout_kernel(prob.handle, inst.N) == kernel
-    p = gpu_params(g, inst)
+    p = gpu_params(g, inst, update=update)
     fit = torch.zeros(inst.N, device="cuda")
     du_out = torch.zeros_like(dev(torch, du_in))
     g.d4orm_denoise_step(prob.handle, p, it, i, dev(torch, u_base), dev(torch, du_in), du_out, fit)
@@ -147,7 +147,7 @@ def _check_step(torch, g, o, inst, it, i, max_oracle_samples=None, seed=0, kerne
     fit_g = host(fit)
     out_g = host(du_out)
     op = oracle_problem(o, inst)
-    pp = oracle_params(o, inst)
+    pp = oracle_params(o, inst, update=update)
     ub64, du64 = u_base.astype(np.float64), du_in.astype(np.float64)
     # per-sample fitness
     if max_oracle_samples and inst.N > max_oracle_samples:
@@ -255,6 +255,68 @@ def test_verdict_unsafe_only_because_of_an_obstacle(torch, g):
         assert v["goal_reached"]
 
 
+MPPI_CASES = [
+    # dyn, integ, n, T, N, it, i, sigma
+    (0, 1, 4, 30, 256, 0, 50, 0.5),
+    (1, 1, 7, 13, 100, 2, 1, 1.0),
+    (2, 1, 8, 40, 300, 1, 99, 0.3),
+    (3, 0, 5, 21, 9000, 0, 10, 0.8),   # N > 8192
+]
+
+
+@pytest.mark.parametrize("kernel", [1, 2], ids=["register", "pipeline"])
+@pytest.mark.parametrize("dyn,integ,n,T,N,it,i,sigma", MPPI_CASES)
+def test_mppi_step_parity(torch, g, oracle_lib, dyn, integ, n, T, N, it, i, sigma, kernel):
+    """The MPPI update rule on the same kernels: constant sigma around the
+    current deformation, new deformation = weighted mean; same fitness and
+    update tolerances as the method's step."""
+    inst = small_instance(dyn, n, T, N, integ=integ, seed=5, K=100)
+    sig = float(np.float32(sigma))
+    r = _check_step(torch, g, oracle_lib, inst, it, i, kernel=kernel, update=(1, sig),
+                    max_oracle_samples=600 if N > 2000 else None)
+    assert r["n_fragile"] <= max(2, 0.05 * min(N, 600))
+
+
+def test_mppi_differs_from_the_schedule(torch, g):
+    """Same samples, same fitness: MPPI's step is not the method's step (the
+    schedule's c, sigma, g differ), and beta0/beta1 do not change MPPI."""
+    inst = small_instance(0, 4, 20, 128, seed=2, K=50)
+    rng = np.random.default_rng(3)
+    ub = dev(torch, scenarios.random_controls(rng, inst, 0.5))
+    du = dev(torch, scenarios.random_deformation(rng, inst))
+    prob = g.Problem(inst)
+    outs = []
+    for update, betas in (((0, 0.0), (1e-4, 1e-2)), ((1, 0.5), (1e-4, 1e-2)), ((1, 0.5), (0.1, 0.3))):
+        p = gpu_params(g, inst, update=update)
+        p.beta0, p.beta1 = betas
+        o = torch.zeros_like(du)
+        g.d4orm_denoise_step(prob.handle, p, 0, 20, ub, du, o, torch.zeros(128, device="cuda"))
+        outs.append(host(o))
+    assert np.abs(outs[0] - outs[1]).max() > 1e-2
+    assert np.array_equal(outs[1], outs[2])
+
+
+def test_mppi_solve_verdict_parity(torch, g, oracle_lib):
+    """A 2-robot swap solved with the MPPI rule by both implementations: the
+    oracle re-judges the GPU's plan with the GPU's verdict, and both reach
+    the same verdict flags."""
+    start = np.array([[-1.5, 0, 0, 0], [1.5, 0, 0, 0]])
+    inst = scenarios.Instance("swap", 0, 1, 2, 60, 0.1, 0.2, (-1.0, -1.0), (1.0, 1.0), 1.0, start, -start,
+                              N=256, K=20, iters=4, seed=0)
+    inst = round_instance(inst)
+    upd = (1, float(np.float32(0.4)))
+    prob = g.Problem(inst)
+    u_out = torch.zeros((inst.T, 2, 2), device="cuda")
+    res = g.d4orm_solve(prob.handle, gpu_params(g, inst, update=upd), g.Budget(max_iters=4), u_out)
+    op = oracle_problem(oracle_lib, inst)
+    _, verdicts, _ = oracle_lib.solve(op, oracle_params(oracle_lib, inst, update=upd), 4)
+    v_g = oracle_lib.verdict(op, inst.w_safe, oracle_lib.rollout(op, host(u_out)))
+    if abs(v_g["min_pair_dist"] - 0.4) > DELTA:
+        assert res["verdict"]["collision_free"] == v_g["collision_free"]
+    assert res["verdict"]["goal_reached"] == v_g["goal_reached"]
+    assert abs(res["verdict"]["reward"] - verdicts[-1]["reward"]) < 0.05
+
+
 @pytest.mark.parametrize("dyn,n,T,N", [(0, 4, 50, 256), (2, 8, 100, 700), (1, 16, 37, 300), (3, 32, 9, 40)])
 def test_rollout_kernels_agree(torch, g, dyn, n, T, N):
     """The register and pipeline kernels evaluate the same samples with the
@@ -331,6 +393,10 @@ def test_denoise_step_argument_errors(torch, g):
     bad.temperature = 0.0
     with pytest.raises(g.D4ormError):
         g.d4orm_denoise_step(prob.handle, bad, 0, 1, a, a, b)
+    for rule, sigma in ((2, 0.5), (1, 0.0), (1, float("nan")), (-1, 0.5)):
+        with pytest.raises(g.D4ormError) as ei:
+            g.d4orm_denoise_step(prob.handle, gpu_params(g, inst, update=(rule, sigma)), 0, 1, a, a, b)
+        assert ei.value.status == 1
 
 
 # ----------------------------------------------------------------------------- solve
