@@ -12,13 +12,22 @@
 //   rollout warp : integrate chunk c - 1 from U[(c - 1) % 2]    -> Pos[(c - 1) % 2]
 //
 // so noise generation and the O(n^2) pair tests (both independent along
-// time) run on the helpers while the recurrence advances.  Per-row sums
-// (one row = one sample at one time step) are reduced inside lane segments
-// in a fixed order and added per sample at the end, so the result is
-// deterministic.  Shared memory holds the mean controls u_base + c dU, two
-// chunks of controls and positions (time-major, rows padded, so that warp
-// accesses are conflict-free) and the per-row terms.
+// time) run on the helpers while the recurrence advances.  There are
+// CT * d_u / 4 helper warps: each helper lane owns one (sample, robot) pair
+// and generates exactly one Philox quad of it per chunk, and scores the
+// time steps h, h + H, ... of the chunk.  Per-row sums (one row = one sample
+// at one time step) are reduced inside lane segments in a fixed order and
+// added per sample at the end, so the result is deterministic.
+//
+// Shared memory: positions Pos[2][CT][SPC][SEG][PD] (PD = 2 in the plane,
+// 4 in space, so a partner pair or a 3D position is one 128-bit load; rows
+// are not padded: every warp access pattern below is conflict-free), the
+// controls U[2][CT][SPC][n][d_u], the mean controls M = u_base + c dU
+// [T][n][d_u] and the per-row terms [SPC][T].  Lanes of padding robots
+// (k >= n) store a far-away sentinel position, so the Eq. (5) indicator of
+// a real robot is "at least two robots (itself included) within 2R + eps".
 #include <cmath>
+#include <cstdint>
 
 #include "d4orm_internal.h"
 
@@ -26,173 +35,260 @@ namespace d4orm {
 
 constexpr int kPipeCT = 16;  // time steps per chunk (a multiple of 4: chunks are Philox-quad aligned)
 
-template <int SEG>
+template <int SEG, int DU>
 struct PipeShape {
     static constexpr int SPC = 32 / SEG;                   // samples per CTA
-    static constexpr int HELPERS = SEG <= 8 ? 3 : 7;       // helper warps
+    static constexpr int HELPERS = kPipeCT * DU / 4;       // helper warps: one quad per lane per chunk
     static constexpr int THREADS = 32 * (1 + HELPERS);
 };
 
-// Shared memory, time-major so that one warp access touches consecutive
-// words: U[2][CT][SPC][n][DU] (controls), Pos[2][CT*SPC][RS] (positions, row
-// stride RS = SEG*DP + 1 so the rows a warp reads fall in different banks),
-// rows[SPC][T] (per-row fitness terms).
-template <int SEG, int DP>
-struct PosStride { static constexpr int RS = SEG * DP + 1; };
+template <int DP>
+struct PosSlot { static constexpr int PD = DP == 2 ? 2 : 4; };  // floats per robot position
 
 template <int DYN, int SEG>
 size_t pipe_smem_bytes(const DevProblem& P)
 {
     using D = DynDims<DYN>;
-    constexpr int SPC = PipeShape<SEG>::SPC;
-    const size_t u = 2ull * SPC * kPipeCT * P.n * D::DU;
-    const size_t pos = 2ull * SPC * kPipeCT * PosStride<SEG, D::DP>::RS;
-    const size_t rows = (size_t)SPC * P.T;
+    constexpr int SPC = PipeShape<SEG, D::DU>::SPC;
+    const size_t pos = 2ull * kPipeCT * SPC * SEG * PosSlot<D::DP>::PD;
+    const size_t u = 2ull * kPipeCT * SPC * P.n * D::DU;
     const size_t mean = (size_t)P.T * P.n * D::DU;
-    return (u + pos + rows + mean) * sizeof(float);
+    const size_t rows = (size_t)SPC * P.T;
+    return (pos + u + mean + rows) * sizeof(float);
+}
+
+// M = u_base + c dU into shared memory: every thread issues up to four
+// 128-bit loads of each input before it stores, so the whole array arrives
+// in one or two L2 round trips (scalar path for unaligned or ragged input).
+__device__ __forceinline__ void stage_mean(float* sM, const float* __restrict__ du_in, const float* __restrict__ u_base,
+                                           float c, int total)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const bool vec = ((((uintptr_t)du_in) | ((uintptr_t)u_base)) & 15u) == 0 && (total & 3) == 0;
+    if (vec) {
+        const int n4 = total >> 2;
+        const float4* d4 = reinterpret_cast<const float4*>(du_in);
+        const float4* b4 = reinterpret_cast<const float4*>(u_base);
+        float4* m4 = reinterpret_cast<float4*>(sM);
+        for (int e0 = tid; e0 < n4; e0 += 4 * nt) {
+            float4 a[4], b[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int e = e0 + r * nt;
+                if (e < n4) {
+                    a[r] = __ldg(d4 + e);
+                    b[r] = __ldg(b4 + e);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int e = e0 + r * nt;
+                if (e < n4)
+                    m4[e] = make_float4(fmaf(c, a[r].x, b[r].x), fmaf(c, a[r].y, b[r].y), fmaf(c, a[r].z, b[r].z),
+                                        fmaf(c, a[r].w, b[r].w));
+            }
+        }
+    } else {
+        for (int e = tid; e < total; e += nt) sM[e] = fmaf(c, du_in[e], u_base[e]);
+    }
 }
 
 template <int DYN, int SEG, bool OBS>
-__global__ void __launch_bounds__(PipeShape<SEG>::THREADS)
+__global__ void __launch_bounds__(PipeShape<SEG, DynDims<DYN>::DU>::THREADS)
 k_rollout_fitness_pipe(const DevProblem P, const DevStep S, const float* __restrict__ u_base,
                        const float* __restrict__ du_in, float* __restrict__ fitness, const int* __restrict__ it_dev)
 {
     using D = DynDims<DYN>;
     constexpr int DX = D::DX, DU = D::DU, DP = D::DP;
-    constexpr int SPC = PipeShape<SEG>::SPC;
-    constexpr int HELPERS = PipeShape<SEG>::HELPERS;
+    constexpr int SPC = PipeShape<SEG, DU>::SPC;
+    constexpr int H = PipeShape<SEG, DU>::HELPERS;
     constexpr int CT = kPipeCT;
-    constexpr int RS = PosStride<SEG, DP>::RS;
-    extern __shared__ float smem[];
+    constexpr int QPC = CT * DU / 4;                       // quads per robot per chunk (= H)
+    constexpr int PD = PosSlot<DP>::PD;
+    constexpr int RS = SEG * PD;                           // floats per position row
+    extern __shared__ float4 smem4[];
+    float* smem = reinterpret_cast<float*>(smem4);
     const int n = P.n, T = P.T;
-    float* sU = smem;                                   // [2][CT][SPC][n][DU]
-    float* sPos = sU + 2 * SPC * CT * n * DU;           // [2][CT*SPC][RS]
-    float* sRows = sPos + 2 * SPC * CT * RS;            // [SPC][T]
-    float* sM = sRows + SPC * T;                         // [T][n][DU] mean controls
-    const int u_slot = SPC * CT * n * DU;
-    const int pos_slot = SPC * CT * RS;
+    const int rowM = n * DU;
+    float* sPos = smem;                                    // [2][CT][SPC][SEG][PD]
+    float* sU = sPos + 2 * CT * SPC * RS;                  // [2][CT][SPC][n][DU]
+    float* sM = sU + 2 * CT * SPC * rowM;                  // [T][n][DU]
+    float* sRows = sM + T * rowM;                          // [SPC][T]
+    const int pos_slot = CT * SPC * RS;
+    const int u_slot = CT * SPC * rowM;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j_base = blockIdx.x * SPC;
     const uint32_t c3 = iter_word(S, it_dev);
     const int nchunks = (T + CT - 1) / CT;
-    const int rowM = n * DU;
-    for (int e = threadIdx.x; e < T * rowM; e += blockDim.x) sM[e] = fmaf(S.c, du_in[e], u_base[e]);
+    stage_mean(sM, du_in, u_base, S.c, T * rowM);
     __syncthreads();
-    const int quads_per_chunk = CT * DU / 4;
 
-    // rollout-warp state (warp 0)
-    const int rk = lane & (SEG - 1);
-    const int rs = lane / SEG;
+    // every lane owns one (sample, robot) pair: s = lane / SEG, k = lane % SEG
+    const int k = lane & (SEG - 1);
+    const int s = lane / SEG;
+    const bool robot = k < n;
+    const int kr = robot ? k : n - 1;
+
+    // rollout-warp state
     float x[DX];
-    load_start<DYN>(x, P, rk);
-    const int rkr = rk < n ? rk : n - 1;
+    load_start<DYN>(x, P, k);
+    const float far = 1.0e15f * (float)(1 + k);   // padding robots park far away and far apart
+    // helper constants: control box, Philox counter words, goal, Eq. (4) normaliser
+    const int h = warp - 1;
+    float lo[DU], hi[DU];
+#pragma unroll
+    for (int d = 0; d < DU; ++d) {
+        lo[d] = P.u_lo[d];
+        hi[d] = P.u_hi[d];
+    }
+    const uint32_t c2 = ((uint32_t)k & 0xffu) | S.c2_step;
+    const uint32_t jj = (uint32_t)(j_base + s);
+    float g[DP];
+#pragma unroll
+    for (int d = 0; d < DP; ++d) g[d] = P.goal[kr * 3 + d];
+    const float inv_d0 = P.inv_d0[kr];
 
     for (int c = 0; c < nchunks + 2; ++c) {
-        if (warp > 0) {
-            const int h = threadIdx.x - 32;  // helper thread index
-            // (1) noise and clipped controls of chunk c
-            if (c < nchunks) {
-                // items over (quad, sample, lane-robot) with the robot
-                // fastest (neighbouring threads touch neighbouring words of U
-                // and of the mean controls); SEG and SPC are powers of two,
-                // so the index split is shifts and masks
-                constexpr int ITEMS = SPC * SEG * (CT * DU / 4);
-                float* U = sU + (c & 1) * u_slot;
-#pragma unroll 1
-                for (int it = h; it < ITEMS; it += 32 * HELPERS) {
-                    const int k = it & (SEG - 1);
-                    const int s = (it / SEG) & (SPC - 1);
-                    const int qq = it / (SEG * SPC);
-                    if (k >= n) continue;
-                    const uint32_t q = (uint32_t)(c * quads_per_chunk + qq);
-                    float z[4];
-                    noise_quad(S, c3, q, (uint32_t)(j_base + s), (uint32_t)k, z);
+        if (warp == 0) {
+            // ---------------- rollout warp: integrate chunk c - 1
+            if (c >= 1 && c <= nchunks) {
+                const int cr = c - 1;
+                const float* U = sU + (cr & 1) * u_slot;
+                float* Pos = sPos + (cr & 1) * pos_slot;
+                const int steps = min(CT, T - cr * CT);
+#pragma unroll 4
+                for (int tl = 0; tl < steps; ++tl) {
+                    float u[DU];
+                    const float* ur = U + (tl * SPC + s) * rowM + kr * DU;
+                    if constexpr (DU == 2) {
+                        const float2 v = *reinterpret_cast<const float2*>(ur);
+                        u[0] = v.x;
+                        u[1] = v.y;
+                    } else {
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        const int e = 4 * (int)q + r;          // element of robot k's stream
-                        const int t = e / DU, d = e - t * DU;
-                        if (t < T) {
-                            U[(((t - c * CT) * SPC + s) * n + k) * DU + d] =
-                                clampf(fmaf(S.sigma, z[r], sM[t * rowM + k * DU + d]), P.u_lo[d], P.u_hi[d]);
+                        for (int d = 0; d < DU; ++d) u[d] = ur[d];
+                    }
+                    integrate<DYN>(x, u, P);
+                    float* pr = Pos + (tl * SPC + s) * RS + k * PD;
+                    if constexpr (PD == 2)
+                        *reinterpret_cast<float2*>(pr) = robot ? make_float2(x[0], x[1]) : make_float2(far, far);
+                    else
+                        *reinterpret_cast<float4*>(pr) =
+                            robot ? make_float4(x[0], x[1], x[2], 0.0f) : make_float4(far, far, far, 0.0f);
+                }
+            }
+        } else {
+            // ---------------- helpers (1): noise and clipped controls of chunk c;
+            // lane (s, k) generates quad h of its robot's stream
+            if (c < nchunks && robot) {
+                const int q = c * QPC + h;
+                if (4 * q < T * DU) {
+                    float z[4];
+                    const U4 w = philox4x32_10(U4{(uint32_t)q, jj, c2, c3}, S);
+                    box_muller(w.x, w.y, z[0], z[1]);
+                    box_muller(w.z, w.w, z[2], z[3]);
+                    float* U = sU + (c & 1) * u_slot;
+                    if constexpr (DU == 2) {
+                        // the quad is time steps 2q, 2q + 1 of controls (0, 1)
+#pragma unroll
+                        for (int r = 0; r < 2; ++r) {
+                            const int t = 2 * q + r;
+                            if (t < T) {
+                                const float2 m = *reinterpret_cast<const float2*>(sM + t * rowM + k * 2);
+                                const float2 v = make_float2(clampf(fmaf(S.sigma, z[2 * r], m.x), lo[0], hi[0]),
+                                                             clampf(fmaf(S.sigma, z[2 * r + 1], m.y), lo[1], hi[1]));
+                                *reinterpret_cast<float2*>(U + ((t - c * CT) * SPC + s) * rowM + k * 2) = v;
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            const int e = 4 * q + r;     // element of robot k's stream
+                            const int t = e / DU, d = e - t * DU;
+                            if (t < T) {
+                                float lod = lo[0], hid = hi[0];
+#pragma unroll
+                                for (int dd = 1; dd < DU; ++dd)
+                                    if (d == dd) {
+                                        lod = lo[dd];
+                                        hid = hi[dd];
+                                    }
+                                U[((t - c * CT) * SPC + s) * rowM + k * DU + d] =
+                                    clampf(fmaf(S.sigma, z[r], sM[t * rowM + k * DU + d]), lod, hid);
+                            }
                         }
                     }
                 }
             }
-            // (2) Eq. (4)/(5) terms of chunk c - 2: one row per lane segment
+            // ---------------- helpers (2): Eq. (4)/(5) terms of chunk c - 2,
+            // time steps h, h + H, ... of the chunk
             const int ce = c - 2;
             if (ce >= 0) {
                 const float* Pos = sPos + (ce & 1) * pos_slot;
-                const int hw = warp - 1;
-                const int k = lane & (SEG - 1);
-                const bool robot = k < n;
-                const int kr = robot ? k : n - 1;
-                float g[DP];
-#pragma unroll
-                for (int d = 0; d < DP; ++d) g[d] = P.goal[kr * 3 + d];
-                const float inv_d0 = P.inv_d0[kr];
-                const int rows = SPC * CT;
-                for (int rb = hw * (32 / SEG); rb < rows; rb += HELPERS * (32 / SEG)) {
-                    const int row = rb + lane / SEG;  // row = tl * SPC + s; warp-uniform loop bound
-                    const int tl = row / SPC, s = row - tl * SPC;
+                for (int tl = h; tl < CT; tl += H) {
                     const int t = ce * CT + tl;
+                    if (t >= T) break;                   // uniform across the warp
+                    const float* pr = Pos + (tl * SPC + s) * RS;
                     float term = 0.0f;
-                    if (row < rows && t < T && robot) {
-                        const float* pr = Pos + row * RS;
+                    if (robot) {
                         float p[DP];
-#pragma unroll
-                        for (int d = 0; d < DP; ++d) p[d] = pr[k * DP + d];
+                        if constexpr (PD == 2) {
+                            const float2 v = *reinterpret_cast<const float2*>(pr + k * 2);
+                            p[0] = v.x;
+                            p[1] = v.y;
+                        } else {
+                            const float4 v = *reinterpret_cast<const float4*>(pr + k * 4);
+                            p[0] = v.x;
+                            p[1] = v.y;
+                            p[2] = v.z;
+                        }
                         float dg2 = 0.0f;
 #pragma unroll
                         for (int d = 0; d < DP; ++d) {
                             const float e = p[d] - g[d];
                             dg2 = fmaf(e, e, dg2);
                         }
-                        bool hit = false;
+                        // Eq. (5): robots within 2R + eps, itself included
+                        int cnt = 0;
+                        if constexpr (PD == 2 && SEG >= 2) {
 #pragma unroll
-                        for (int l = 0; l < SEG; ++l) {
-                            float d2 = 0.0f;
-#pragma unroll
-                            for (int d = 0; d < DP; ++d) {
-                                const float e = p[d] - pr[l * DP + d];
-                                d2 = fmaf(e, e, d2);
+                            for (int m = 0; m < SEG / 2; ++m) {
+                                const float4 v = *reinterpret_cast<const float4*>(pr + 4 * m);
+                                const float ax = p[0] - v.x, ay = p[1] - v.y;
+                                const float bx = p[0] - v.z, by = p[1] - v.w;
+                                cnt += fmaf(ay, ay, ax * ax) <= P.thr2;
+                                cnt += fmaf(by, by, bx * bx) <= P.thr2;
                             }
-                            hit |= (l != k) & (l < n) & (d2 <= P.thr2);
+                        } else if constexpr (PD == 2) {
+                            cnt = 1;                      // a single robot
+                        } else {
+#pragma unroll
+                            for (int l = 0; l < SEG; ++l) {
+                                const float4 v = *reinterpret_cast<const float4*>(pr + 4 * l);
+                                const float ax = p[0] - v.x, ay = p[1] - v.y, az = p[2] - v.z;
+                                cnt += fmaf(az, az, fmaf(ay, ay, ax * ax)) <= P.thr2;
+                            }
                         }
-                        term = (1.0f - sqrt_approx(dg2) * inv_d0) - (hit ? S.w_safe : 0.0f);
+                        term = (1.0f - sqrt_approx(dg2) * inv_d0) - (cnt > 1 ? S.w_safe : 0.0f);
                         // Appendix: binary obstacle penalty with the same weight
                         if constexpr (OBS)
                             if (obstacle_hit<DP>(P, p)) term -= S.w_safe;
                     }
                     term = seg_sum<SEG>(term);
-                    if (k == 0 && row < rows && t < T) sRows[s * T + t] = term;
+                    if (k == 0) sRows[s * T + t] = term;
                 }
-            }
-        } else if (c >= 1 && c <= nchunks) {
-            // (3) rollout of chunk c - 1
-            const int cr = c - 1;
-            const float* U = sU + (cr & 1) * u_slot;
-            float* Pos = sPos + (cr & 1) * pos_slot;
-            const int steps = min(CT, T - cr * CT);
-#pragma unroll 4
-            for (int tl = 0; tl < steps; ++tl) {
-                float u[DU];
-#pragma unroll
-                for (int d = 0; d < DU; ++d) u[d] = U[((tl * SPC + rs) * n + rkr) * DU + d];
-                integrate<DYN>(x, u, P);
-#pragma unroll
-                for (int d = 0; d < DP; ++d) Pos[(tl * SPC + rs) * RS + rk * DP + d] = x[d];
             }
         }
         __syncthreads();
     }
     // per-sample sum of the row terms, fixed order
     if (warp == 0) {
-        for (int s = 0; s < SPC; ++s) {
+        for (int ss = 0; ss < SPC; ++ss) {
             float a = 0.0f;
-            for (int t = lane; t < T; t += 32) a += sRows[s * T + t];
+            for (int t = lane; t < T; t += 32) a += sRows[ss * T + t];
             a = seg_sum<32>(a);
-            if (lane == 0 && j_base + s < S.N) fitness[j_base + s] = a * P.inv_nT;
+            if (lane == 0 && j_base + ss < S.N) fitness[j_base + ss] = a * P.inv_nT;
         }
     }
 }
@@ -208,9 +304,9 @@ template <int DYN, int SEG, bool OBS>
 static cudaError_t launch_pipe(const DevProblem& P, const DevStep& S, const float* u_base, const float* du_in,
                                float* fitness, const int* it_dev, cudaStream_t st)
 {
-    constexpr int SPC = PipeShape<SEG>::SPC;
-    const int grid = (S.N + SPC - 1) / SPC;
-    k_rollout_fitness_pipe<DYN, SEG, OBS><<<grid, PipeShape<SEG>::THREADS, pipe_smem_bytes<DYN, SEG>(P), st>>>(
+    using Shape = PipeShape<SEG, DynDims<DYN>::DU>;
+    const int grid = (S.N + Shape::SPC - 1) / Shape::SPC;
+    k_rollout_fitness_pipe<DYN, SEG, OBS><<<grid, Shape::THREADS, pipe_smem_bytes<DYN, SEG>(P), st>>>(
         P, S, u_base, du_in, fitness, it_dev);
     return cudaGetLastError();
 }
@@ -270,10 +366,11 @@ size_t rollout_fitness_pipe_smem(const DevProblem& P)
 {
     const int seg = P.n <= 1 ? 1 : P.n <= 2 ? 2 : P.n <= 4 ? 4 : P.n <= 8 ? 8 : P.n <= 16 ? 16 : 32;
     const int spc = 32 / seg;
-    const size_t u = 2ull * spc * kPipeCT * P.n * P.d_u;
-    const size_t pos = 2ull * spc * kPipeCT * (seg * P.d_p + 1);
+    const int pd = P.d_p == 2 ? 2 : 4;
+    const size_t pos = 2ull * kPipeCT * spc * seg * pd;
+    const size_t u = 2ull * kPipeCT * spc * P.n * P.d_u;
     const size_t mean = (size_t)P.T * P.n * P.d_u;
-    return (u + pos + (size_t)spc * P.T + mean) * sizeof(float);
+    return (pos + u + mean + (size_t)spc * P.T) * sizeof(float);
 }
 
 }  // namespace d4orm
