@@ -272,6 +272,59 @@ __device__ __forceinline__ void load_start(float* x, const DevProblem& P, int k)
     for (int c = 0; c < DX; ++c) x[c] = P.start[kk * DX + c];
 }
 
+// M = base + c dU into shared memory by the whole CTA.  Every thread issues
+// up to four 128-bit loads of each input before it stores, so the array
+// arrives in one or two round trips to L2 instead of one per element; a
+// scalar tail covers lengths that are not a multiple of four, and unaligned
+// inputs take the scalar path.  NC: the inputs are read-only for the whole
+// kernel, so the non-coherent read path may be used.
+template <bool NC>
+__device__ __forceinline__ float ld_in(const float* p)
+{
+    if constexpr (NC) return __ldg(p);
+    else return *p;
+}
+template <bool NC>
+__device__ __forceinline__ float4 ld_in4(const float4* p)
+{
+    if constexpr (NC) return __ldg(p);
+    else return *p;
+}
+
+template <bool NC>
+__device__ __forceinline__ void stage_mean(float* sM, const float* du, const float* base, float c, int total)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const bool vec = ((((uintptr_t)du) | ((uintptr_t)base) | ((uintptr_t)sM)) & 15u) == 0;
+    if (!vec) {
+        for (int e = tid; e < total; e += nt) sM[e] = fmaf(c, ld_in<NC>(du + e), ld_in<NC>(base + e));
+        return;
+    }
+    const int n4 = total >> 2;
+    const float4* d4 = reinterpret_cast<const float4*>(du);
+    const float4* b4 = reinterpret_cast<const float4*>(base);
+    float4* m4 = reinterpret_cast<float4*>(sM);
+    for (int e0 = tid; e0 < n4; e0 += 4 * nt) {
+        float4 a[4], b[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int e = e0 + r * nt;
+            if (e < n4) {
+                a[r] = ld_in4<NC>(d4 + e);
+                b[r] = ld_in4<NC>(b4 + e);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int e = e0 + r * nt;
+            if (e < n4)
+                m4[e] = make_float4(fmaf(c, a[r].x, b[r].x), fmaf(c, a[r].y, b[r].y), fmaf(c, a[r].z, b[r].z),
+                                    fmaf(c, a[r].w, b[r].w));
+        }
+    }
+    for (int e = 4 * n4 + tid; e < total; e += nt) sM[e] = fmaf(c, ld_in<NC>(du + e), ld_in<NC>(base + e));
+}
+
 // Warp-wide sums within aligned segments of SEG lanes.
 template <int SEG>
 __device__ __forceinline__ float seg_sum(float v)

@@ -73,7 +73,7 @@ __device__ __noinline__ void batched_instance(const DevProblem& P, const BatchIn
             S.w_safe = C.w_safe;
             S.inv_lambda = C.inv_lambda;
             // mean controls M = tau.u + c dU_i
-            for (int e = tid; e < nctrl; e += nt) sM[e] = fmaf(S.c, du[cur][e], tau[e]);
+            stage_mean<false>(sM, du[cur], tau, S.c, nctrl);  // written by this CTA: coherent loads
             __syncthreads();
             // fitness of all N samples, 32/SEG per warp per pass
             constexpr int SPW = 32 / SEG;

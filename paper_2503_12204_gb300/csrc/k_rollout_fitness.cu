@@ -37,7 +37,7 @@ k_rollout_fitness(const DevProblem P, const DevStep S, const float* __restrict__
     extern __shared__ float sM[];  // M[t][k][d]
 
     const int nctrl = P.T * P.n * DU;
-    for (int e = threadIdx.x; e < nctrl; e += blockDim.x) sM[e] = fmaf(S.c, du_in[e], u_base[e]);
+    stage_mean<true>(sM, du_in, u_base, S.c, nctrl);
     __syncthreads();
 
     const int lane = threadIdx.x & 31;

@@ -57,42 +57,6 @@ size_t pipe_smem_bytes(const DevProblem& P)
     return (pos + u + mean + rows) * sizeof(float);
 }
 
-// M = u_base + c dU into shared memory: every thread issues up to four
-// 128-bit loads of each input before it stores, so the whole array arrives
-// in one or two L2 round trips (scalar path for unaligned or ragged input).
-__device__ __forceinline__ void stage_mean(float* sM, const float* __restrict__ du_in, const float* __restrict__ u_base,
-                                           float c, int total)
-{
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const bool vec = ((((uintptr_t)du_in) | ((uintptr_t)u_base)) & 15u) == 0 && (total & 3) == 0;
-    if (vec) {
-        const int n4 = total >> 2;
-        const float4* d4 = reinterpret_cast<const float4*>(du_in);
-        const float4* b4 = reinterpret_cast<const float4*>(u_base);
-        float4* m4 = reinterpret_cast<float4*>(sM);
-        for (int e0 = tid; e0 < n4; e0 += 4 * nt) {
-            float4 a[4], b[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int e = e0 + r * nt;
-                if (e < n4) {
-                    a[r] = __ldg(d4 + e);
-                    b[r] = __ldg(b4 + e);
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int e = e0 + r * nt;
-                if (e < n4)
-                    m4[e] = make_float4(fmaf(c, a[r].x, b[r].x), fmaf(c, a[r].y, b[r].y), fmaf(c, a[r].z, b[r].z),
-                                        fmaf(c, a[r].w, b[r].w));
-            }
-        }
-    } else {
-        for (int e = tid; e < total; e += nt) sM[e] = fmaf(c, du_in[e], u_base[e]);
-    }
-}
-
 template <int DYN, int SEG, bool OBS>
 __global__ void __launch_bounds__(PipeShape<SEG, DynDims<DYN>::DU>::THREADS)
 k_rollout_fitness_pipe(const DevProblem P, const DevStep S, const float* __restrict__ u_base,
@@ -121,7 +85,7 @@ k_rollout_fitness_pipe(const DevProblem P, const DevStep S, const float* __restr
     const int j_base = blockIdx.x * SPC;
     const uint32_t c3 = iter_word(S, it_dev);
     const int nchunks = (T + CT - 1) / CT;
-    stage_mean(sM, du_in, u_base, S.c, T * rowM);
+    stage_mean<true>(sM, du_in, u_base, S.c, T * rowM);
     __syncthreads();
 
     // every lane owns one (sample, robot) pair: s = lane / SEG, k = lane % SEG
