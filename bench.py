@@ -82,6 +82,16 @@ def flops_per_sample_rollout(inst) -> int:
     return inst.T * (inst.n * per_robot + inst.n * (inst.n - 1) // 2 * per_pair + inst.n * n_obs * (3 * d_p + 1))
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# dominant kernel, from one ncu --set full capture of the kernel as it is now
+# (summaries and commands in profiles/); a kernel changed since its capture
+# must be dropped from this table (its traffic is then reported as null).
+NCU_TRAFFIC_BYTES = {
+    ("k_rollout_fitness_pipe", "unicycle_n8_T100_N2048"): 38400,
+    ("k_rollout_fitness", "holo3d_n16_T100_N8192"): 77568,
+}
+
+
 def fp32_peak_tflops(sm_count: int, clock_mhz: float) -> float:
     # 128 FP32 lanes per SM, FFMA = 2 flops
     return sm_count * 128 * 2 * clock_mhz * 1e6 / 1e12
@@ -202,7 +212,7 @@ def cpu_oracle_rate(inst, budget_s: float = 15.0, n_sample: int | None = None) -
         t_total += time.perf_counter() - t0
         done += n_sample
         reps += 1
-    return {"value": done / t_total, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": done / t_total, "unit": UNIT, "cores": 1, "kind": "oracle", "samples": done,
             "sample": f"{reps} denoising step(s) of {n_sample} of the {inst.N} samples of {inst.name} "
                       f"(fitness + weights + update, FP64, 1 thread), {t_total:.1f} s"}
 
@@ -291,6 +301,16 @@ def run_batched(args, torch, g, world, rank):
     peak = fp32_peak_tflops(props.multi_processor_count, 2070.0)
     achieved = flops / args.steps / (ms / 1e3) / 1e12
     solved = sum(1 for r in results if r["first_success_iter"] >= 0)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle on a bounded sample of the batch: one denoising step of
+        # 2 s over the first samples of every 64th problem
+        picks = insts[::64]
+        parts = [cpu_oracle_rate(i, budget_s=2.0) for i in picks]
+        secs = sum(p_["samples"] / p_["value"] for p_ in parts)
+        cpu = {"value": sum(p_["samples"] for p_ in parts) / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{len(picks)} of the 512 problems (every 64th), one denoising step over their first "
+                         f"samples each, FP64, 1 thread, {secs:.1f} s"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -312,6 +332,8 @@ def run_batched(args, torch, g, world, rank):
         "median_ms_to_success": statistics.median([r["ms_to_success"] for r in results if r["ms_to_success"] > 0])
         if solved else None,
     }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
     if rank == 0:
         print(json.dumps(line), flush=True)
     g.d4orm_batch_destroy(batch)
@@ -463,7 +485,7 @@ def run_ours(args):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": csum,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": NCU_TRAFFIC_BYTES.get((k2_name, inst.name)),
                      "kernel": k2_name, "peak_basis": "FP32 lanes x 2 x 2070 MHz (152 SMs x 128)",
                      "flops_per_launch": flops, "launch_ms": k2_ms},
         "kernel_share": {"rollout_fitness": share[0], "softmax_weights": share[1], "weighted_sum": share[2],
