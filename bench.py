@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="unicycle_n8",
-                    choices=sorted(scenarios.WORKLOADS) + ["mixed512", "warmstart"])
+                    choices=sorted(scenarios.WORKLOADS) + ["mixed512", "warmstart", "mppi_compare"])
     ap.add_argument("--teams", type=int, default=200, help="held-out teams for --workload warmstart")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -339,6 +339,40 @@ def run_batched(args, torch, g, world, rank):
     g.d4orm_batch_destroy(batch)
 
 
+def run_mppi_compare(args, torch, g, world, rank):
+    """Mean time to the first feasible plan (collision-free, every robot within
+    0.5 m of its goal) of the method and of MPPI on the same kernels: 16 2D
+    holonomic robots on a 4 m antipodal circle (|a| <= 2, |v| <= 1.5),
+    N = 2048, 100 steps per iteration, stop on success, 5 s deadline, at most
+    50 iterations, --teams evaluation seeds, for each (w, lambda) of a small
+    grid (the paper leaves both open); MPPI's sigma is tuned per setting on 8
+    other seeds.  One problem at a time on the whole GPU.  The line's value
+    is the method's mean time at w = 1, lambda = 0.3."""
+    from paper_2503_12204_gb300 import compare as C
+    inst = scenarios.holo2d_circle(16, 4.0, a_max=2.0, v_max=1.5)
+    inst.goal_tol = 0.5
+    grid = []
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        for w, lam in C.SETTINGS:
+            res = C.compare(torch, inst, 2048, 100, args.teams, C.SIGMAS, w_safe=w, temperature=lam,
+                            log=lambda m: None)
+            grid.append({"w": w, "lambda": lam, "method": res["method"], "mppi": res["mppi"],
+                         "mppi_sigma": res["mppi_sigma"], "speedup_mean_ms": res.get("speedup_mean_ms")})
+    primary = next(r for r in grid if r["w"] == 1.0 and r["lambda"] == 0.3)
+    line = {
+        "metric": "mean ms to first feasible plan (method vs MPPI, same kernels)",
+        "value": primary["method"].get("mean_ms"), "unit": "ms", "n_gpus": world, "steps": args.teams, "warmup": 1,
+        "ms_per_step": primary["method"].get("mean_ms"), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": inst.name, "robots": 16, "samples_N": 2048, "denoise_steps": 100,
+                   "max_iterations": 50, "deadline_ms": 5000, "goal_tol_m": inst.goal_tol,
+                   "mppi_sigma_candidates": list(C.SIGMAS), "settings_w_lambda": [list(x) for x in C.SETTINGS]},
+        "grid": grid, "clocks": clocks.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_warmstart(args, torch, g, world, rank):
     """Median time to a collision-free plan with every robot within 0.5 m of
     its goal, learned warm start vs the plain method, on held-out random 2D
@@ -389,8 +423,9 @@ def run_ours(args):
     barrier(torch, world)
     import paper_2503_12204_gb300 as g
 
-    if args.workload in ("mixed512", "warmstart"):
-        (run_batched if args.workload == "mixed512" else run_warmstart)(args, torch, g, world, rank)
+    if args.workload in ("mixed512", "warmstart", "mppi_compare"):
+        {"mixed512": run_batched, "warmstart": run_warmstart, "mppi_compare": run_mppi_compare}[args.workload](
+            args, torch, g, world, rank)
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()

@@ -150,6 +150,16 @@ _DYN_DEFAULTS = {
 }
 
 
+def holo2d_circle(n: int = 16, r: float = 4.0, N: int = 2048, a_max: float = 1.0, v_max: float = 1.0) -> Instance:
+    """n 2D holonomic robots evenly spaced on a circle of radius r with
+    antipodal goals (Sec. V-A), RK4 dt 0.1, T = 100 (H = 100, dt = 0.1 as in
+    Sec. V), R_a 0.2 m, |a| <= a_max, |v| <= v_max, N samples, 100 steps."""
+    p = circle_antipodal(n, r)
+    s, g = _full_state(HOLO2D, p, -p)
+    return Instance(f"holo2d_circle_n{n}_r{r:g}_a{a_max:g}_v{v_max:g}_T100_N{N}", HOLO2D, RK4, n, 100, 0.1, 0.2,
+                    (-a_max, -a_max), (a_max, a_max), v_max, s, g, N=N, K=100, iters=50, seed=0)
+
+
 def circle_obstacles_n16(n_obstacles: int = 4, N: int = 4096) -> Instance:
     """16 2D holonomic robots on a circle of radius 4 m with antipodal goals
     (Sec. V-A layout) and 1..4 static disc obstacles of radius 0.4 m across
