@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="unicycle_n8",
-                    choices=sorted(scenarios.WORKLOADS) + ["mixed512", "warmstart", "mppi_compare"])
+                    choices=sorted(scenarios.WORKLOADS) + ["mixed512", "warmstart", "mppi_compare", "sensitivity"])
     ap.add_argument("--teams", type=int, default=200, help="held-out teams for --workload warmstart")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -373,6 +373,30 @@ def run_mppi_compare(args, torch, g, world, rank):
         print(json.dumps(line), flush=True)
 
 
+def run_sensitivity(args, torch, g, world, rank):
+    """Success rate against denoising steps K (50, 100, 200) and iterations
+    (1..5) for 10 and 16 robots of each dynamics, --teams runs each (seeds),
+    every (dynamics, robots, K) one batched persistent launch; w = 1,
+    lambda = 0.3, goals judged at 0.5 m.  The line's value is the 16-robot
+    2D holonomic success rate within 5 iterations at K = 100."""
+    from paper_2503_12204_gb300 import sweep as SW
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        rows = SW.sweep(torch, runs=args.teams, log=lambda m: None)
+    primary = next(r for r in rows if r["dynamics"] == "holo2d" and r["robots"] == 16 and r["steps"] == 100)
+    line = {
+        "metric": "success rate within 5 iterations (16 robots, 2D holonomic, K=100)",
+        "value": primary["success_within_iters"][-1], "unit": "fraction", "n_gpus": world, "steps": args.teams,
+        "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "sensitivity_K_x_iterations", "runs": args.teams, "samples_N": 2048,
+                   "steps_K": [50, 100, 200], "max_iterations": 5, "robots": [10, 16],
+                   "dynamics": list(SW.DYNAMICS), "w": 1.0, "lambda": 0.3, "goal_tol_m": 0.5},
+        "table": rows, "clocks": clocks.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_warmstart(args, torch, g, world, rank):
     """Median time to a collision-free plan with every robot within 0.5 m of
     its goal, learned warm start vs the plain method, on held-out random 2D
@@ -423,9 +447,9 @@ def run_ours(args):
     barrier(torch, world)
     import paper_2503_12204_gb300 as g
 
-    if args.workload in ("mixed512", "warmstart", "mppi_compare"):
-        {"mixed512": run_batched, "warmstart": run_warmstart, "mppi_compare": run_mppi_compare}[args.workload](
-            args, torch, g, world, rank)
+    if args.workload in ("mixed512", "warmstart", "mppi_compare", "sensitivity"):
+        {"mixed512": run_batched, "warmstart": run_warmstart, "mppi_compare": run_mppi_compare,
+         "sensitivity": run_sensitivity}[args.workload](args, torch, g, world, rank)
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()
