@@ -42,6 +42,33 @@ __device__ float block_reduce(float v, float* sh)
     return r;
 }
 
+// Block-wide sum and maximum in one round (sh: at least 66 floats).
+__device__ __forceinline__ void block_reduce_sum_max(float& s, float& m, float* sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    s = warp_sum(s);
+    m = warp_max(m);
+    if (lane == 0) {
+        sh[warp] = s;
+        sh[33 + warp] = m;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        float a = lane < nw ? sh[lane] : 0.0f;
+        float b = lane < nw ? sh[33 + lane] : -INFINITY;
+        a = warp_sum(a);
+        b = warp_max(b);
+        if (lane == 0) {
+            sh[32] = a;
+            sh[65] = b;
+        }
+    }
+    __syncthreads();
+    s = sh[32];
+    m = sh[65];
+    __syncthreads();
+}
+
 // Samples whose unnormalised weight exp(l_j - max l) falls below 2^-36
 // are left out of the weighted sum: together they move it by at most
 // N * 2^-36 * max|eps| / Z (under 1e-6 of the largest weight for N <= 65536),
@@ -54,7 +81,7 @@ constexpr float kLogWeightCut = -24.953298f;  // -36 ln 2
 // Batch normalisation (Sec. IV-C) + temperature softmax (Eq. (6)) of the N
 // rewards in `fitness` (global or shared memory), by the whole thread block:
 // writes the ordered (weight, index) list of the samples that carry weight
-// and its length.  sh[33], scan[33]: shared scratch.  VR > 0 keeps each
+// and its length.  sh[66], scan[33]: shared scratch.  VR > 0 keeps each
 // thread's (at most VR) values in registers.
 // ---------------------------------------------------------------------------
 template <int VR>
@@ -83,9 +110,15 @@ __device__ __forceinline__ void softmax_block(const float* __restrict__ fitness,
             for (int i = 0; i < cnt; ++i) f(i, fitness[j0 + i]);
         }
     };
-    float s = 0.0f;
-    each([&](int, float x) { s += x; });
-    const float mu = block_reduce<false>(s, sh) / (float)N;
+    // sum and largest reward in one reduction: the largest logit is the
+    // logit of the largest reward, (x - mu) * scale being monotone in x
+    float s = 0.0f, mx = -INFINITY;
+    each([&](int, float x) {
+        s += x;
+        mx = fmaxf(mx, x);
+    });
+    block_reduce_sum_max(s, mx, sh);
+    const float mu = s / (float)N;
     float v = 0.0f;
     each([&](int, float x) {
         const float d = x - mu;
@@ -94,9 +127,7 @@ __device__ __forceinline__ void softmax_block(const float* __restrict__ fitness,
     const float sd = sqrtf(block_reduce<false>(v, sh) / (float)N);
     const bool degenerate = !(sd > 1e-12f * fmaxf(1.0f, fabsf(mu)));
     const float scale = degenerate ? 0.0f : inv_lambda / sd;
-    float m = -INFINITY;
-    each([&](int, float x) { m = fmaxf(m, (x - mu) * scale); });
-    m = block_reduce<true>(m, sh);
+    const float m = (mx - mu) * scale;
     float z = 0.0f;
     int kept = 0;
     each([&](int, float x) {

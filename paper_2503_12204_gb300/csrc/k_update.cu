@@ -16,6 +16,7 @@
 // Pass 3 (k_finalize): dU_{i-1} = g_i (c_i dU_i + sigma_i sum_chunks S_c),
 // the weighted mean of the samples of Eq. (12) scaled as in Eq. (13); chunk
 // partials are added in a fixed order, so the result is deterministic.
+#include <algorithm>
 #include <cmath>
 
 #include "d4orm_internal.h"
@@ -32,7 +33,7 @@ __global__ void __launch_bounds__(kSoftmaxThreads)
 k_softmax_weights(const float* __restrict__ fitness, int N, float inv_lambda, float2* __restrict__ list,
                   int* __restrict__ count, float* __restrict__ stats)
 {
-    __shared__ float sh[33];
+    __shared__ float sh[66];
     __shared__ int scan[33];
     softmax_block<VR>(fitness, N, inv_lambda, list, count, stats, sh, scan);
 }
@@ -128,10 +129,13 @@ SumSplit plan_weighted_sum(const DevProblem& P, int N, int sm_count)
 cudaError_t launch_softmax_weights(const float* fitness, int N, float inv_lambda, float2* list, int* count,
                                    float* stats, cudaStream_t st)
 {
-    if (N <= 8 * kSoftmaxThreads)
-        k_softmax_weights<8><<<1, kSoftmaxThreads, 0, st>>>(fitness, N, inv_lambda, list, count, stats);
-    else
+    if (N <= 8 * kSoftmaxThreads) {
+        // eight rewards per thread: fewer warps, cheaper block reductions
+        const int threads = std::min(kSoftmaxThreads, std::max(128, ((N + 7) / 8 + 31) / 32 * 32));
+        k_softmax_weights<8><<<1, threads, 0, st>>>(fitness, N, inv_lambda, list, count, stats);
+    } else {
         k_softmax_weights<0><<<1, kSoftmaxThreads, 0, st>>>(fitness, N, inv_lambda, list, count, stats);
+    }
     return cudaGetLastError();
 }
 
