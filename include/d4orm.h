@@ -211,6 +211,18 @@ d4orm_status d4orm_denoise_step(d4orm_problem *problem, const d4orm_params *para
                                 const float *u_base_dev, const float *du_in_dev, float *du_out_dev,
                                 float *fitness_dev, void *stream);
 
+/* The first half of denoising step i on its own: the N samples of Eq. (12),
+ * their rollouts and their Eq. (3) fitness r_j (Algorithm 1, sampling,
+ * rollout and reward lines), with no weights and no update.  The values
+ * are those d4orm_denoise_step writes to fitness_dev for the same
+ * arguments.  u_base_dev, du_in_dev: [T][n][d_u]; fitness_dev: float[N]
+ * (required).  The call allocates nothing after the problem's first step
+ * of this N and makes no synchronising call, so it can be captured in a
+ * CUDA graph.  Errors: as d4orm_denoise_step. */
+d4orm_status d4orm_sample_fitness(d4orm_problem *problem, const d4orm_params *params, int iter, int step_i,
+                                  const float *u_base_dev, const float *du_in_dev, float *fitness_dev,
+                                  void *stream);
+
 /* d4orm_denoise_step with a CUDA event recorded on `stream` between its
  * kernels; synchronises and writes the device time of each kernel, in ms,
  * to kernel_ms_host[4]: {rollout+fitness, softmax weights, weighted noise

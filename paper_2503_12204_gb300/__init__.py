@@ -37,7 +37,7 @@ STATUS = {0: "D4ORM_OK", 1: "D4ORM_ERR_INVALID_ARG", 2: "D4ORM_ERR_UNSUPPORTED",
 # Every entry point declared in include/d4orm.h.
 EXPORTS = (
     "d4orm_problem_create", "d4orm_problem_destroy", "d4orm_problem_set_rollout_kernel",
-    "d4orm_problem_rollout_kernel", "d4orm_rollout", "d4orm_denoise_step",
+    "d4orm_problem_rollout_kernel", "d4orm_rollout", "d4orm_sample_fitness", "d4orm_denoise_step",
     "d4orm_denoise_step_timed", "d4orm_denoise_step_noalloc", "d4orm_solve",
     "d4orm_sample_noise", "d4orm_philox4x32_10", "d4orm_status_string", "d4orm_last_error",
     "d4orm_batch_create", "d4orm_batch_solve", "d4orm_batch_info", "d4orm_batch_destroy", "d4orm_solve_batched",
@@ -123,6 +123,8 @@ def _load() -> ctypes.CDLL:
     lib.d4orm_problem_rollout_kernel.restype = i
     lib.d4orm_rollout.argtypes = [vp, ctypes.POINTER(_Params), vp, vp, ctypes.POINTER(_Verdict), vp]
     lib.d4orm_rollout.restype = i
+    lib.d4orm_sample_fitness.argtypes = [vp, ctypes.POINTER(_Params), i, i, vp, vp, vp, vp]
+    lib.d4orm_sample_fitness.restype = i
     lib.d4orm_denoise_step.argtypes = [vp, ctypes.POINTER(_Params), i, i, vp, vp, vp, vp, vp]
     lib.d4orm_denoise_step.restype = i
     lib.d4orm_denoise_step_timed.argtypes = [vp, ctypes.POINTER(_Params), i, i, vp, vp, vp, vp,
@@ -292,6 +294,14 @@ def d4orm_rollout(handle, params: Params | None, u_dev, states_dev=None, want_ve
     _check(lib.d4orm_rollout(handle, ctypes.byref(pc) if pc is not None else None, _ptr(u_dev), _ptr(states_dev),
                              ctypes.byref(v) if want_verdict else None, _stream(stream)))
     return _verdict(v) if want_verdict else None
+
+
+def d4orm_sample_fitness(handle, params: Params, iter: int, step_i: int, u_base_dev, du_in_dev, fitness_dev,
+                         stream=None) -> None:
+    """Eq. (3) fitness of the N samples of step i (no update)."""
+    pc = params.c()
+    _check(lib.d4orm_sample_fitness(handle, ctypes.byref(pc), iter, step_i, _ptr(u_base_dev), _ptr(du_in_dev),
+                                    _ptr(fitness_dev), _stream(stream)))
 
 
 def d4orm_denoise_step(handle, params: Params, iter: int, step_i: int, u_base_dev, du_in_dev, du_out_dev,

@@ -506,6 +506,24 @@ d4orm_status d4orm_denoise_step(d4orm_problem* P, const d4orm_params* params, in
     return enqueue_step(P, S, u_base_dev, du_in_dev, du_out_dev, fitness_dev, nullptr, (cudaStream_t)stream);
 }
 
+d4orm_status d4orm_sample_fitness(d4orm_problem* P, const d4orm_params* params, int iter, int step_i,
+                                  const float* u_base_dev, const float* du_in_dev, float* fitness_dev, void* stream)
+{
+    d4orm_status s = check_params(P, params);
+    if (s != D4ORM_OK) return s;
+    if (!u_base_dev || !du_in_dev || !fitness_dev) return fail(D4ORM_ERR_INVALID_ARG, "null device buffer");
+    if (step_i < 1 || step_i > params->n_steps) return fail(D4ORM_ERR_INVALID_ARG, "step_i out of 1..K");
+    if (iter < 0 || iter >= D4ORM_MAX_ITERS) return fail(D4ORM_ERR_INVALID_ARG, "iter out of range");
+    s = ensure_workspace(P, params->n_samples);
+    if (s != D4ORM_OK) return s;
+    std::vector<double> abar;
+    schedule(params, abar);
+    const DevStep S = step_consts(params, abar, iter, step_i);
+    D4_CUDA(launch_rollout_fitness(P->dp, S, u_base_dev, du_in_dev, fitness_dev, nullptr, P->sm_count,
+                                   P->rollout_kernel, (cudaStream_t)stream));
+    return D4ORM_OK;
+}
+
 d4orm_status d4orm_solve(d4orm_problem* P, const d4orm_params* params, const d4orm_budget* budget,
                          const float* du_init_dev, float* u_out_dev, d4orm_result* out_host, void* stream)
 {

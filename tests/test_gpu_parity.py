@@ -317,6 +317,33 @@ def test_mppi_solve_verdict_parity(torch, g, oracle_lib):
     assert abs(res["verdict"]["reward"] - verdicts[-1]["reward"]) < 0.05
 
 
+@pytest.mark.parametrize("kernel", [1, 2], ids=["register", "pipeline"])
+@pytest.mark.parametrize("dyn,n,T,N", [(0, 5, 23, 300), (2, 8, 40, 257), (1, 3, 17, 64)])
+def test_sample_fitness_entry_point(torch, g, oracle_lib, dyn, n, T, N, kernel):
+    """d4orm_sample_fitness writes exactly the fitness the full step writes,
+    and those values match the oracle within the step's tolerance."""
+    inst = small_instance(dyn, n, T, N, seed=9, K=30)
+    rng = np.random.default_rng(4)
+    ub = scenarios.random_controls(rng, inst, 0.5).astype(np.float32)
+    du = scenarios.random_deformation(rng, inst).astype(np.float32)
+    prob = g.Problem(inst)
+    g.d4orm_problem_set_rollout_kernel(prob.handle, kernel)
+    p = gpu_params(g, inst)
+    f1 = torch.zeros(N, device="cuda")
+    f2 = torch.zeros(N, device="cuda")
+    g.d4orm_sample_fitness(prob.handle, p, 3, 17, dev(torch, ub), dev(torch, du), f1)
+    g.d4orm_denoise_step(prob.handle, p, 3, 17, dev(torch, ub), dev(torch, du), torch.zeros_like(dev(torch, du)), f2)
+    torch.cuda.synchronize()
+    assert torch.equal(f1, f2)
+    f_o, _, frag = oracle_lib.sample_fitness(oracle_problem(oracle_lib, inst), oracle_params(oracle_lib, inst), 3, 17,
+                                             ub.astype(np.float64), du.astype(np.float64), np.arange(N), delta=DELTA,
+                                             with_fragile=True)
+    tol = 1e-3 * np.abs(f_o) + 1e-5 + frag * inst.w_safe / (n * T)
+    assert (np.abs(host(f1) - f_o) <= tol).all()
+    with pytest.raises(g.D4ormError):
+        g.d4orm_sample_fitness(prob.handle, p, 0, 0, dev(torch, ub), dev(torch, du), f1)
+
+
 @pytest.mark.parametrize("dyn,n,T,N", [(0, 4, 50, 256), (2, 8, 100, 700), (1, 16, 37, 300), (3, 32, 9, 40)])
 def test_rollout_kernels_agree(torch, g, dyn, n, T, N):
     """The register and pipeline kernels evaluate the same samples with the
