@@ -173,12 +173,27 @@ def barrier(torch, world):
 
 
 def max_over_ranks(torch, world, value: float) -> float:
+    """The largest value over all ranks (the job's time is its slowest rank)."""
     if world == 1:
         return value
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    device = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_instance(inst, rank: int):
+    """Rank r solves its own replica of the workload: the same problem with
+    instance tag r, so every rank draws its own noise (no data-path
+    exchange; the job's throughput is the sum over ranks)."""
+    inst.tag = rank
+    return inst
+
+
+def job_throughput(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Whole-job units per second: every rank's units over the slowest rank's time."""
+    return units_per_rank * world / (max_ms / 1e3)
 
 
 def cpu_oracle_rate(inst, budget_s: float = 15.0, n_sample: int | None = None) -> dict:
@@ -308,7 +323,7 @@ def run_batched(args, torch, g, world, rank):
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     ms = max_over_ranks(torch, world, ms)
     per_step = rollouts / args.steps
-    value = per_step * world / (ms / 1e3)
+    value = job_throughput(per_step, world, ms)
     # end to end: descriptors from host arrays, solve, plans read back
     u_host = [torch.empty(o.shape, dtype=torch.float32).pin_memory() for o in outs]
     e2e = []
@@ -483,8 +498,7 @@ def run_ours(args):
             import torch.distributed as dist
             dist.destroy_process_group()
         return
-    inst = f32_inst(scenarios.WORKLOADS[args.workload]())
-    inst.tag = rank  # each rank solves its own replica
+    inst = replica_instance(f32_inst(scenarios.WORKLOADS[args.workload]()), rank)
     d_x, d_u, d_p = inst.dims
     prob = g.Problem(inst)
     params = g.Params(n_samples=inst.N, n_steps=inst.K, temperature=inst.lam, w_safe=inst.w_safe,
@@ -515,7 +529,7 @@ def run_ours(args):
     barrier(torch, world)
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     ms = max_over_ranks(torch, world, ms)
-    value = rollouts_per_step * world / (ms / 1e3)
+    value = job_throughput(rollouts_per_step, world, ms)
 
     # ---------------- end to end through the C ABI with host buffers
     start_h = torch.tensor(inst.start, dtype=torch.float32).pin_memory()

@@ -1,0 +1,59 @@
+"""The experiment drivers (method-vs-MPPI comparison, sensitivity sweep):
+host logic on the CPU, and one tiny end-to-end run of each on the GPU."""
+import numpy as np
+import pytest
+
+import scenarios
+
+
+def test_summarize_counts_and_means():
+    from paper_2503_12204_gb300 import compare as C
+    rows = [dict(ok=True, first=2, ms=30.0, reward=0.5, collision_free=True, max_goal_dist=0.2),
+            dict(ok=False, first=-1, ms=None, reward=0.1, collision_free=False, max_goal_dist=3.0),
+            dict(ok=True, first=0, ms=10.0, reward=0.7, collision_free=True, max_goal_dist=0.4)]
+    s = C.summarize(rows)
+    assert s["runs"] == 3 and abs(s["success_rate"] - 2 / 3) < 1e-12
+    assert s["mean_ms"] == 20.0 and s["median_ms"] == 20.0
+    assert s["mean_iterations"] == 2.0                     # first success at iterations 3 and 1
+    assert abs(s["final_collision_free_rate"] - 2 / 3) < 1e-12
+    assert s["median_final_max_goal_dist"] == 0.4
+    assert C.summarize([])["success_rate"] == 0.0
+
+
+@pytest.mark.parametrize("dyn", ["holo2d", "holo3d", "diffdrive4"])
+def test_sweep_instances(dyn):
+    from paper_2503_12204_gb300 import sweep as SW
+    inst = SW.instance(dyn, 10, 512)
+    d_x, d_u, d_p = inst.dims
+    assert inst.n == 10 and inst.T == 100 and inst.N == 512 and inst.goal_tol == 0.5
+    # antipodal: every goal is the reflection of its start through the centre
+    assert np.allclose(inst.goal[:, :d_p], -inst.start[:, :d_p], atol=1e-6)
+    assert np.allclose(np.linalg.norm(inst.start[:, :d_p], axis=1), 4.0, atol=1e-5)
+    # inputs are already binary32 values
+    assert np.array_equal(inst.start, inst.start.astype(np.float32).astype(np.float64))
+
+
+def test_holo2d_circle_limits():
+    inst = scenarios.holo2d_circle(16, 4.0, a_max=2.0, v_max=1.5)
+    assert inst.u_lo == (-2.0, -2.0) and inst.u_hi == (2.0, 2.0) and inst.v_max == 1.5
+    assert inst.start.shape == (16, 4)
+
+
+@pytest.mark.gpu
+def test_compare_and_sweep_run_on_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("CUDA device required")
+    from helpers import build_library
+    build_library()
+    from paper_2503_12204_gb300 import compare as C
+    from paper_2503_12204_gb300 import sweep as SW
+    inst = scenarios.holo2d_circle(4, 1.5, a_max=2.0, v_max=1.5)
+    inst.goal_tol = 0.5
+    res = C.compare(torch, inst, 256, 20, 2, (0.1, 0.3), max_iters=3, tune_runs=2, w_safe=1.0, temperature=0.3,
+                    log=lambda m: None)
+    assert res["method"]["runs"] == 2 and res["mppi"]["runs"] == 2 and res["mppi_sigma"] in (0.1, 0.3)
+    rows = SW.sweep(torch, dynamics=("holo2d",), robots=(4,), steps=(20,), runs=3, max_iters=2, N=256,
+                    log=lambda m: None)
+    assert len(rows) == 1 and len(rows[0]["success_within_iters"]) == 2
+    assert rows[0]["success_within_iters"][0] <= rows[0]["success_within_iters"][1]
