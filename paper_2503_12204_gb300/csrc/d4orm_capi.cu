@@ -60,10 +60,13 @@ void default_box(int dyn, float* lo, float* hi)
     }
 }
 
+// One iteration shape of a problem: captured into a graph the second time
+// it is requested (the first request runs it eagerly, so a one-off solve
+// does not pay for capture and instantiation).
 struct GraphEntry {
     int i0 = 0;
     bool record_all = false;
-    cudaGraphExec_t exec = nullptr;
+    cudaGraphExec_t exec = nullptr;  // null: seen once, not captured yet
 };
 
 }  // namespace
@@ -245,18 +248,55 @@ bool same_params(const d4orm_params& a, const d4orm_params& b)
 // iteration-end apply/rollout/verdict, and the verdict read-back, captured
 // once into a graph.  The iteration index is read from P->d_it, which the
 // verdict kernel increments, so one graph serves every iteration.
+// The kernels of one iteration of Algorithm 2 on stream st: steps i0..1,
+// then apply + rollout + verdict (K4, which also advances the device
+// iteration counter), then, unless every verdict is kept on the device,
+// the read-back of this iteration's verdict.
+d4orm_status enqueue_iteration(d4orm_problem* P, const d4orm_params* p, const std::vector<double>& abar, int i0,
+                               bool record_all, cudaStream_t st)
+{
+    int cur = 0;
+    for (int i = i0; i >= 1; --i) {
+        const DevStep S = step_consts(p, abar, 0, i);
+        const d4orm_status status = enqueue_step(P, S, P->d_tau_u, P->d_du[cur], P->d_du[cur ^ 1], nullptr, P->d_it, st);
+        if (status != D4ORM_OK) return status;
+        cur ^= 1;
+    }
+    // verdict slot: d_verdicts[it] when recording all, else slot 0
+    cudaError_t e = launch_apply_rollout_verdict(P->dp, p->w_safe, P->d_tau_u, P->d_du[cur], P->d_tau_u, nullptr,
+                                                 P->d_verdicts, P->d_it, st);
+    if (e != cudaSuccess) return cuda_fail(e, "launch_apply_rollout_verdict");
+    if (!record_all) {
+        e = cudaMemcpyAsync(P->h_verdicts, P->d_verdicts, sizeof(d4orm_verdict), cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(verdict)");
+    }
+    return D4ORM_OK;
+}
+
+// The executable graph of one iteration shape, or null (*out) the first
+// time the shape is requested: the caller then enqueues it eagerly.
 d4orm_status iteration_graph(d4orm_problem* P, const d4orm_params* p, const std::vector<double>& abar, int i0,
                              bool record_all, cudaStream_t st, cudaGraphExec_t* out)
 {
+    *out = nullptr;
     if (!same_params(P->g_params, *p)) {
         free_graphs(P);
         P->g_params = *p;
     }
+    GraphEntry* entry = nullptr;
     for (auto& g : P->graphs)
-        if (g.i0 == i0 && g.record_all == record_all) {
-            *out = g.exec;
-            return D4ORM_OK;
-        }
+        if (g.i0 == i0 && g.record_all == record_all) entry = &g;
+    if (!entry) {
+        GraphEntry ge;
+        ge.i0 = i0;
+        ge.record_all = record_all;
+        P->graphs.push_back(ge);
+        return D4ORM_OK;
+    }
+    if (entry->exec) {
+        *out = entry->exec;
+        return D4ORM_OK;
+    }
     cudaStream_t cap;
     D4_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
@@ -266,22 +306,7 @@ d4orm_status iteration_graph(d4orm_problem* P, const d4orm_params* p, const std:
         cudaStreamDestroy(cap);
         return cuda_fail(e, "cudaStreamBeginCapture");
     }
-    int cur = 0;
-    for (int i = i0; i >= 1 && status == D4ORM_OK; --i) {
-        const DevStep S = step_consts(p, abar, 0, i);
-        status = enqueue_step(P, S, P->d_tau_u, P->d_du[cur], P->d_du[cur ^ 1], nullptr, P->d_it, cap);
-        cur ^= 1;
-    }
-    if (status == D4ORM_OK) {
-        // verdict slot: d_verdicts[it] when recording all, else slot 0
-        e = launch_apply_rollout_verdict(P->dp, p->w_safe, P->d_tau_u, P->d_du[cur], P->d_tau_u, nullptr, P->d_verdicts,
-                                         P->d_it, cap);
-        if (e != cudaSuccess) status = cuda_fail(e, "launch_apply_rollout_verdict");
-    }
-    if (status == D4ORM_OK && !record_all) {
-        e = cudaMemcpyAsync(P->h_verdicts, P->d_verdicts, sizeof(d4orm_verdict), cudaMemcpyDeviceToHost, cap);
-        if (e != cudaSuccess) status = cuda_fail(e, "cudaMemcpyAsync(verdict)");
-    }
+    status = enqueue_iteration(P, p, abar, i0, record_all, cap);
     e = cudaStreamEndCapture(cap, &graph);
     if (status == D4ORM_OK && e != cudaSuccess) status = cuda_fail(e, "cudaStreamEndCapture");
     cudaStreamDestroy(cap);
@@ -293,11 +318,7 @@ d4orm_status iteration_graph(d4orm_problem* P, const d4orm_params* p, const std:
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-    GraphEntry ge;
-    ge.i0 = i0;
-    ge.record_all = record_all;
-    ge.exec = exec;
-    P->graphs.push_back(ge);
+    entry->exec = exec;
     *out = exec;
     return D4ORM_OK;
 }
@@ -560,7 +581,12 @@ d4orm_status d4orm_solve(d4orm_problem* P, const d4orm_params* params, const d4o
         cudaGraphExec_t exec = nullptr;
         s = iteration_graph(P, params, abar, i0, !per_iter_sync, st, &exec);
         if (s != D4ORM_OK) return s;
-        D4_CUDA(cudaGraphLaunch(exec, st));
+        if (exec) {
+            D4_CUDA(cudaGraphLaunch(exec, st));
+        } else {
+            s = enqueue_iteration(P, params, abar, i0, !per_iter_sync, st);
+            if (s != D4ORM_OK) return s;
+        }
         if (!per_iter_sync) {
             // keep this iteration's verdict: slot 0 -> history slot 1 + it
             D4_CUDA(cudaMemcpyAsync(P->d_verdicts + 1 + it, P->d_verdicts, sizeof(d4orm_verdict),

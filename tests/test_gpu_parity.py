@@ -436,7 +436,12 @@ def test_solve_matches_eager_steps(torch, g):
     p = gpu_params(g, inst)
     nctrl = (inst.T, inst.n, 2)
     u_out = torch.zeros(nctrl, device="cuda")
+    # a new handle runs its first iteration eagerly and captures the graph
+    # the second time: both forms give the same bits
+    g.d4orm_solve(prob.handle, p, g.Budget(max_iters=1), u_out)
+    first = u_out.clone()
     res = g.d4orm_solve(prob.handle, p, g.Budget(max_iters=1), u_out)
+    assert torch.equal(first, u_out)
     zero = torch.zeros(nctrl, device="cuda")
     du = torch.zeros(nctrl, device="cuda")
     for i in range(inst.K, 0, -1):
@@ -451,6 +456,28 @@ def test_solve_matches_eager_steps(torch, g):
     assert res["iters_run"] == 1
     v = g.d4orm_rollout(prob.handle, p, u_out)
     assert v == res["verdict"]
+
+
+@pytest.mark.parametrize("stop", [False, True])
+def test_solve_eager_then_graph_iterations(torch, g, stop):
+    """Three iterations on a new handle (the first eager, the second captured
+    and replayed, the third replayed) equal three iterations on a handle
+    whose graph is already captured, bit for bit, verdicts included."""
+    inst = small_instance(2, 5, 30, 200, seed=3, K=15)
+    p = gpu_params(g, inst)
+    budget = g.Budget(max_iters=3, stop_on_success=stop, deadline_ms=0.0)
+    outs, results = [], []
+    for _ in range(2):
+        prob = g.Problem(inst)
+        u = torch.zeros((inst.T, inst.n, 2), device="cuda")
+        if results:  # second handle: capture first
+            g.d4orm_solve(prob.handle, p, g.Budget(max_iters=2, stop_on_success=stop), u)
+        results.append(g.d4orm_solve(prob.handle, p, budget, u))
+        outs.append(u)
+    torch.cuda.synchronize()
+    assert torch.equal(outs[0], outs[1])
+    assert results[0]["verdict"] == results[1]["verdict"]
+    assert results[0]["iters_run"] == results[1]["iters_run"]
 
 
 def test_solve_verdict_parity_holo2d_n4(torch, g, oracle_lib):
