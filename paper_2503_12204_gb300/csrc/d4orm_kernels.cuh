@@ -199,6 +199,12 @@ __device__ __forceinline__ float sample_fitness_segment(const DevProblem& P, con
 
     float x[DX];
     load_start<DYN>(x, P, k);
+    // padding robots park far away and far apart, so no pair test involving
+    // them can hit and the Eq. (5) test needs no validity mask
+    if (!robot) {
+#pragma unroll
+        for (int d = 0; d < DP; ++d) x[d] = 1.0e15f * (float)(1 + k);
+    }
     float g[DP];
 #pragma unroll
     for (int d = 0; d < DP; ++d) g[d] = P.goal[kr * 3 + d];
@@ -207,59 +213,71 @@ __device__ __forceinline__ float sample_fitness_segment(const DevProblem& P, con
     const int rowM = P.n * DU;
     const float* Mk = sM + kr * DU;
     float acc = 0.0f;
-    // pair (k, k+s mod SEG) exists when both robots are real
-    bool pair_ok[SEG / 2 > 0 ? SEG / 2 : 1];
+    // bit of the lane that tests pair (k - s, k), for s = 1..SEG/2 - 1
+    uint32_t back[SEG / 2 > 1 ? SEG / 2 - 1 : 1];
 #pragma unroll
-    for (int s = 1; s <= SEG / 2; ++s) pair_ok[s - 1] = robot && (((k + s) & (SEG - 1)) < P.n);
+    for (int s = 1; s < SEG / 2; ++s) back[s - 1] = (uint32_t)(seg_base + ((k - s) & (SEG - 1)));
 
-    for (int t0 = 0; t0 < P.T; t0 += 4) {
-        float eps[4 * DU];
+    // one time step t with its noise eps[d]
+    auto step = [&](int t, const float* eps) {
+        float u[DU];
+#pragma unroll
+        for (int d = 0; d < DU; ++d)
+            u[d] = clampf(fmaf(S.sigma, eps[d], Mk[t * rowM + d]), P.u_lo[d], P.u_hi[d]);
+        integrate<DYN>(x, u, P);
+        // Eq. (4): goal term
+        float dg2 = 0.0f;
+#pragma unroll
+        for (int d = 0; d < DP; ++d) {
+            const float e = x[d] - g[d];
+            dg2 = fmaf(e, e, dg2);
+        }
+        // Eq. (5): any partner inside 2R+eps.  Each unordered pair is
+        // evaluated once: lane k tests partner k+s (mod SEG) for
+        // s = 1..SEG/2, and a ballot hands the flag to the partner (for
+        // s = SEG/2 both lanes of the pair test it).
+        bool hit = false;
+#pragma unroll
+        for (int s = 1; s <= SEG / 2; ++s) {
+            const int src = seg_base + ((k + s) & (SEG - 1));
+            float d2 = 0.0f;
+#pragma unroll
+            for (int d = 0; d < DP; ++d) {
+                const float e = x[d] - __shfl_sync(kFull, x[d], src);
+                d2 = fmaf(e, e, d2);
+            }
+            const bool h = d2 <= P.thr2;
+            hit |= h;
+            if (2 * s != SEG) {
+                const unsigned m = __ballot_sync(kFull, h);
+                hit |= (m >> back[s - 1]) & 1u;
+            }
+        }
+        if (robot) acc += (1.0f - sqrt_approx(dg2) * inv_d0) - (hit ? w_safe : 0.0f);
+        // Appendix: binary obstacle penalty with the same weight
+        if constexpr (OBS)
+            if (robot && obstacle_hit<DP>(P, x)) acc -= w_safe;
+    };
+    // the noise of four time steps, d_u Philox quads
+    auto noise4 = [&](int t0, float* eps) {
         const uint32_t q0 = (uint32_t)(t0 * DU) >> 2;
 #pragma unroll
         for (int c = 0; c < DU; ++c) noise_quad(S, c3, q0 + c, (uint32_t)j, (uint32_t)k, &eps[4 * c]);
+    };
+
+    const int T4 = P.T & ~3;
+    for (int t0 = 0; t0 < T4; t0 += 4) {  // whole groups of four: no per-step bound test
+        float eps[4 * DU];
+        noise4(t0, eps);
 #pragma unroll
-        for (int tt = 0; tt < 4; ++tt) {
-            const int t = t0 + tt;
-            if (t < P.T) {  // uniform across the warp
-                float u[DU];
+        for (int tt = 0; tt < 4; ++tt) step(t0 + tt, &eps[tt * DU]);
+    }
+    if (T4 < P.T) {  // ragged tail, uniform across the warp
+        float eps[4 * DU];
+        noise4(T4, eps);
 #pragma unroll
-                for (int d = 0; d < DU; ++d)
-                    u[d] = clampf(fmaf(S.sigma, eps[tt * DU + d], Mk[t * rowM + d]), P.u_lo[d], P.u_hi[d]);
-                integrate<DYN>(x, u, P);
-                // Eq. (4): goal term
-                float dg2 = 0.0f;
-#pragma unroll
-                for (int d = 0; d < DP; ++d) {
-                    const float e = x[d] - g[d];
-                    dg2 = fmaf(e, e, dg2);
-                }
-                // Eq. (5): any partner inside 2R+eps.  Each unordered pair
-                // is evaluated once: lane k tests partner k+s (mod SEG) for
-                // s = 1..SEG/2, and a ballot hands the flag to the partner
-                // (for s = SEG/2 both lanes of the pair test it).
-                bool hit = false;
-#pragma unroll
-                for (int s = 1; s <= SEG / 2; ++s) {
-                    const int src = seg_base + ((k + s) & (SEG - 1));
-                    float d2 = 0.0f;
-#pragma unroll
-                    for (int d = 0; d < DP; ++d) {
-                        const float e = x[d] - __shfl_sync(kFull, x[d], src);
-                        d2 = fmaf(e, e, d2);
-                    }
-                    const bool h = pair_ok[s - 1] & (d2 <= P.thr2);
-                    hit |= h;
-                    if (2 * s != SEG) {
-                        const unsigned m = __ballot_sync(kFull, h);
-                        hit |= (m >> (seg_base + ((k - s) & (SEG - 1)))) & 1u;
-                    }
-                }
-                if (robot) acc += (1.0f - sqrt_approx(dg2) * inv_d0) - (hit ? w_safe : 0.0f);
-                // Appendix: binary obstacle penalty with the same weight
-                if constexpr (OBS)
-                    if (robot && obstacle_hit<DP>(P, x)) acc -= w_safe;
-            }
-        }
+        for (int tt = 0; tt < 3; ++tt)
+            if (T4 + tt < P.T) step(T4 + tt, &eps[tt * DU]);
     }
     acc = seg_sum<SEG>(acc);
     return acc * P.inv_nT;
