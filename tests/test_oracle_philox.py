@@ -3,8 +3,10 @@
 * Philox is pinned bit-exactly against an independent implementation of
   Philox4x32-10 (Salmon et al., SC'11): cuRAND's host-side generator
   (CURAND_RNG_PSEUDO_PHILOX4_32_10), whose output quad m (for the layout it
-  uses) is Philox(counter=(m >> 16, 0, m & 0xffff, 0), key=(seed lo, seed hi)).
-  That mapping covers both key words, counter words 0 and 2 and every round.
+  uses) is Philox(counter=((m >> 16) mod 2^32, m >> 48, m & 0xffff, 0),
+  key=(seed lo, seed hi)).  That mapping covers both key words, counter
+  words 0, 1 and 2 and every round; word 3 is pinned on the GPU against
+  cuRAND's device generator (tests/test_gpu_philox_device.py).
 * Box-Muller is pinned by distribution tests against the standard normal
   (moments and Kolmogorov-Smirnov) and by its two exact points.
 """
@@ -53,12 +55,14 @@ def test_philox_matches_curand_host(oracle_lib, seed):
         assert np.array_equal(got, ref[4 * m: 4 * m + 4]), (seed, m)
 
 
-@pytest.mark.parametrize("quad", [65535, 65536, 65537, 1000 * 65536 + 5, (2**32 - 1) * 65536 + 65535])
+@pytest.mark.parametrize("quad", [65535, 65536, 65537, 1000 * 65536 + 5, (2**32 - 1) * 65536 + 65535,
+                                  2**48 + 5, 3 * 2**48 + 7 * 65536 + 11, 2**61 + 12345])
 def test_philox_matches_curand_high_counter_words(oracle_lib, quad):
+    """Quads at and beyond 2^48 carry into counter word 1 (m >> 48)."""
     seed = 0x0123456789ABCDEF
     key = (seed & 0xFFFFFFFF, seed >> 32)
     ref = _curand_host(seed, 4 * quad, 4)
-    got = oracle_lib.philox4x32_10((quad >> 16, 0, quad & 0xFFFF, 0), key)
+    got = oracle_lib.philox4x32_10(((quad >> 16) & 0xFFFFFFFF, quad >> 48, quad & 0xFFFF, 0), key)
     assert np.array_equal(got, ref)
 
 
