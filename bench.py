@@ -89,6 +89,7 @@ def flops_per_sample_rollout(inst) -> int:
 NCU_TRAFFIC_BYTES = {
     ("k_rollout_fitness_pipe", "unicycle_n8_T100_N2048"): 38400,
     ("k_rollout_fitness", "holo3d_n16_T100_N8192"): 88576,
+    ("k_rollout_fitness", "unicycle_n8_T100_N2048"): 46080,
 }
 
 

@@ -171,7 +171,9 @@ void d4orm_problem_destroy(d4orm_problem *problem);
  * shuffles.  PIPELINE: one rollout warp per 32/SEG samples plus helper warps
  * that generate the noise of the next time chunk and score the previous one
  * (for batches too small to fill the GPU with the register kernel).  AUTO
- * picks by batch size.  Both compute the same fitness (summation order
+ * picks PIPELINE when the register kernel would have fewer than 2.5 warps
+ * per SM, else REGISTER (the pipelined kernel also needs its shared memory
+ * to fit in 200 KB).  Both compute the same fitness (summation order
  * aside). */
 typedef enum {
     D4ORM_ROLLOUT_AUTO = 0,

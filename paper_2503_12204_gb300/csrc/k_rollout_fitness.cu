@@ -148,11 +148,14 @@ int resolve_rollout_kernel(const DevProblem& P, int N, int sm_count, int request
     const bool pipe_fits = rollout_fitness_pipe_smem(P) <= 200 * 1024;
     if (requested == D4ORM_ROLLOUT_PIPELINE && pipe_fits) return D4ORM_ROLLOUT_PIPELINE;
     if (requested == D4ORM_ROLLOUT_REGISTER || !pipe_fits) return D4ORM_ROLLOUT_REGISTER;
-    // automatic: the register kernel needs about eight warps per SM to hide
-    // its per-step latency; smaller batches expose parallelism along time
+    // automatic: below about 2.5 warps per SM the register kernel leaves
+    // the SMs too idle and the pipelined kernel's parallelism along time
+    // wins (measured whole solves on GB300: unicycle, 8 robots, N = 1024 /
+    // 1.7 warps per SM: pipelined 12.6 vs register 13.4 ms; N = 2048 / 3.4
+    // warps per SM: register 14.3 vs pipelined 16.7 ms)
     const int seg = P.n <= 1 ? 1 : P.n <= 2 ? 2 : P.n <= 4 ? 4 : P.n <= 8 ? 8 : P.n <= 16 ? 16 : 32;
     const long long warps = ((long long)N * seg + 31) / 32;
-    return warps < 8LL * sm_count ? D4ORM_ROLLOUT_PIPELINE : D4ORM_ROLLOUT_REGISTER;
+    return 2 * warps < 5LL * sm_count ? D4ORM_ROLLOUT_PIPELINE : D4ORM_ROLLOUT_REGISTER;
 }
 
 cudaError_t launch_rollout_fitness(const DevProblem& P, const DevStep& S, const float* u_base, const float* du_in,
