@@ -385,6 +385,19 @@ def test_denoise_step_parity_full_size(torch, g, oracle_lib, name, it, i, cap):
     _check_step(torch, g, oracle_lib, inst, it, i, max_oracle_samples=cap, seed=1)
 
 
+def test_denoise_step_at_the_control_size_limit(torch, g, oracle_lib):
+    """T * n * d_u = D4ORM_MAX_CTRL (32 robots, 768 steps, 2 controls): the
+    register kernel stages 192 KB of mean controls (200 KB opt-in), AUTO
+    picks it because the pipelined kernel's shared memory would not fit,
+    and the step matches the oracle on a sample of the batch."""
+    inst = small_instance(0, 32, 768, 64, seed=5, K=10)
+    assert inst.T * inst.n * 2 == g.MAX_CTRL
+    prob = g.Problem(inst)
+    assert g.d4orm_problem_rollout_kernel(prob.handle, inst.N) == g.ROLLOUT_REGISTER
+    r = _check_step(torch, g, oracle_lib, inst, 0, 7, max_oracle_samples=12, seed=2)
+    assert r["checked"] == 12
+
+
 @pytest.mark.parametrize("kernel", [1, 2])
 def test_denoise_step_is_deterministic(torch, g, kernel):
     inst = small_instance(1, 9, 40, 1000, seed=5)
