@@ -122,17 +122,38 @@ d4orm_status ensure_workspace(d4orm_problem* P, int N)
     if (s != D4ORM_OK) return s;
     const size_t nctrl = (size_t)P->T * P->n * P->d_u;
     if (!P->d_tau_u) {
-        if (cudaMalloc(&P->d_tau_u, nctrl * sizeof(float)) != cudaSuccess ||
-            cudaMalloc(&P->d_du[0], nctrl * sizeof(float)) != cudaSuccess ||
-            cudaMalloc(&P->d_du[1], nctrl * sizeof(float)) != cudaSuccess ||
-            cudaMalloc(&P->d_stats, 4 * sizeof(float)) != cudaSuccess ||
-            cudaMalloc(&P->d_count, sizeof(int)) != cudaSuccess ||
-            cudaMalloc(&P->d_it, sizeof(int)) != cudaSuccess ||
-            cudaMalloc(&P->d_verdicts, (1 + D4ORM_MAX_ITERS) * sizeof(d4orm_verdict)) != cudaSuccess ||
-            cudaMallocHost(&P->h_verdicts, (1 + D4ORM_MAX_ITERS) * sizeof(d4orm_verdict)) != cudaSuccess) {
+        // all or nothing: a partial set would leave the next call with null
+        // buffers behind a non-null d_tau_u
+        float *tau = nullptr, *du0 = nullptr, *du1 = nullptr, *stats = nullptr;
+        int *count = nullptr, *it = nullptr;
+        d4orm_verdict *verdicts = nullptr, *h_verdicts = nullptr;
+        if (cudaMalloc(&tau, nctrl * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&du0, nctrl * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&du1, nctrl * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&stats, 4 * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&count, sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&it, sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&verdicts, (1 + D4ORM_MAX_ITERS) * sizeof(d4orm_verdict)) != cudaSuccess ||
+            cudaMallocHost(&h_verdicts, (1 + D4ORM_MAX_ITERS) * sizeof(d4orm_verdict)) != cudaSuccess) {
             cudaGetLastError();
+            cudaFree(tau);
+            cudaFree(du0);
+            cudaFree(du1);
+            cudaFree(stats);
+            cudaFree(count);
+            cudaFree(it);
+            cudaFree(verdicts);
+            cudaFreeHost(h_verdicts);
             return fail(D4ORM_ERR_OOM, "workspace allocation failed");
         }
+        P->d_tau_u = tau;
+        P->d_du[0] = du0;
+        P->d_du[1] = du1;
+        P->d_stats = stats;
+        P->d_count = count;
+        P->d_it = it;
+        P->d_verdicts = verdicts;
+        P->h_verdicts = h_verdicts;
     }
     if (N > P->ws_N) {
         free_graphs(P);
