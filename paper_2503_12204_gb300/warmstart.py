@@ -22,8 +22,9 @@ import time
 import numpy as np
 
 from . import (Budget, Params, Problem, WarmStartDesc, d4orm_batch_create, d4orm_batch_destroy, d4orm_batch_solve,
-               d4orm_warmstart_create, d4orm_warmstart_features, d4orm_warmstart_get_params,
-               d4orm_warmstart_predict, d4orm_warmstart_set_params, d4orm_warmstart_train_step)
+               d4orm_warmstart_create, d4orm_warmstart_destroy, d4orm_warmstart_features,
+               d4orm_warmstart_get_params, d4orm_warmstart_predict, d4orm_warmstart_set_params,
+               d4orm_warmstart_train_step)
 
 MAGIC = b"D4WS"
 
@@ -197,8 +198,15 @@ def main():
     ap.add_argument("--eval-samples", type=int, default=4096)
     ap.add_argument("--start-step", type=int, default=30)
     ap.add_argument("--out", default=".")
+    ap.add_argument("--eval-only", metavar="WEIGHTS", default=None,
+                    help="skip data generation and training: evaluate these weights on the held-out teams")
+    ap.add_argument("--min-robots", type=int, default=0, help="held-out teams with at least this many robots")
+    ap.add_argument("--max-teams", type=int, default=0, help="at most this many held-out teams (0: all)")
     args = ap.parse_args()
     os.makedirs(args.out, exist_ok=True)
+    if args.eval_only:
+        evaluate_only(torch, args)
+        return
     log_f = open(os.path.join(args.out, "warmstart_log.txt"), "w")
 
     def log(msg):
@@ -227,6 +235,30 @@ def main():
     res.update(dataset=int(solved), train_steps=args.steps, train_seconds=train_s, loss_curve=curve[::10])
     with open(os.path.join(args.out, "warmstart_eval.json"), "w") as f:
         json.dump(res, f)
+
+
+def held_out_teams(count: int, min_robots: int = 0, max_teams: int = 0):
+    """The held-out teams (seed 4), optionally only those with at least
+    min_robots robots, and at most max_teams of them."""
+    teams = [t for t in scenarios_set(count, seed=4) if t.n >= min_robots]
+    return teams[:max_teams] if max_teams > 0 else teams
+
+
+def evaluate_only(torch, args):
+    """Evaluate saved weights (no data generation, no training)."""
+    torch.cuda.set_device(0)
+    desc, params_np, meta = load_weights(args.eval_only)
+    desc.max_batch = 1
+    ws = d4orm_warmstart_create(desc)
+    d4orm_warmstart_set_params(ws, params_np)
+    held = held_out_teams(args.held_out, args.min_robots, args.max_teams)
+    res, rows = evaluate(torch, ws, held, Params(n_samples=args.eval_samples, n_steps=100, seed=4, instance_tag=0),
+                         args.start_step, args.eval_iters, log=print)
+    d4orm_warmstart_destroy(ws)
+    res.update(teams=len(held), min_robots=args.min_robots, eval_iters=args.eval_iters, weights_meta=meta)
+    with open(os.path.join(args.out, "warmstart_eval_only.json"), "w") as f:
+        json.dump(res, f)
+    print(json.dumps({"all": res["all"], "n16": res["n16"]}))
 
 
 def scenarios_set(count, seed):

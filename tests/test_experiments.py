@@ -57,3 +57,15 @@ def test_compare_and_sweep_run_on_gpu():
                     log=lambda m: None)
     assert len(rows) == 1 and len(rows[0]["success_within_iters"]) == 2
     assert rows[0]["success_within_iters"][0] <= rows[0]["success_within_iters"][1]
+
+
+def test_held_out_team_selection():
+    """The evaluation-only mode's team filter: held-out teams (seed 4) with at
+    least min_robots robots, at most max_teams of them, in order."""
+    from paper_2503_12204_gb300 import warmstart as W
+    all_teams = W.held_out_teams(120)
+    big = W.held_out_teams(120, min_robots=15, max_teams=4)
+    assert len(all_teams) == 120
+    assert [t.n for t in big] == [t.n for t in all_teams if t.n >= 15][:4]
+    assert all(t.n >= 15 for t in big)
+
