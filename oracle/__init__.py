@@ -50,10 +50,12 @@ def build(force: bool = False) -> str:
         os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "d4orm_oracle.h"))
     ):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(
-            ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared",
-             "-o", tmp, _SRC, "-lm"]
-        )
+        base = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        # OpenMP splits independent samples (fitness) and robots (weighted
+        # mean) over threads; every sum keeps its order, so the results do
+        # not depend on the thread count.  Without OpenMP the loops run serially.
+        if subprocess.call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL) != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -117,6 +119,8 @@ def _load():
         lib.orc_denoise_step.argtypes = [P(_Problem), P(_Params), ctypes.c_int, ctypes.c_int, d, d, d, d, d, d]
         lib.orc_weighted_update.argtypes = [P(_Problem), P(_Params), ctypes.c_int, ctypes.c_int, d, d, d]
         lib.orc_apply.argtypes = [P(_Problem), d, d, d]
+        lib.orc_set_threads.argtypes = [ctypes.c_int]
+        lib.orc_max_threads.restype = ctypes.c_int
         lib.orc_solve.argtypes = [P(_Problem), P(_Params), ctypes.c_int, ctypes.c_int, ctypes.c_int, d, d,
                                   P(_Verdict), i32]
         lib.orc_solve.restype = ctypes.c_int
@@ -370,3 +374,12 @@ def solve(prob: Problem, params: Params, max_iters: int, stop_on_success: bool =
                      reward=v.reward, objective=v.objective, min_pair_dist=v.min_pair_dist)
                 for v in list(vs)[: iters.value]]
     return u_out, verdicts, first
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's parallel sample loops (1 = serial)."""
+    _load().orc_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(_load().orc_max_threads())

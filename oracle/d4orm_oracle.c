@@ -374,6 +374,12 @@ static void step_scales(const orc_params *pp, const double *abar, int i, double 
  *   dU_j ~ N(dU_i / sqrt(abar_i), (1/abar_i - 1) I),
  * drawn as dU_i / sqrt(abar_i) + sqrt(1/abar_i - 1) * eps_j
  * (MPPI: dU_i + sigma * eps_j). */
+static double sample_entry(const orc_params *pp, int it, int i, int j, int k, int e, double du,
+                           double mean_scale, double sd)
+{
+    return du * mean_scale + sd * orc_noise(pp, it, i, j, k, e);
+}
+
 static void make_sample(const orc_problem *p, const orc_params *pp, int it, int i, int j,
                         const double *abar, const double *du_in, double *sample)
 {
@@ -385,7 +391,7 @@ static void make_sample(const orc_problem *p, const orc_params *pp, int it, int 
         for (int k = 0; k < p->n; ++k)
             for (int d = 0; d < d_u; ++d) {
                 size_t idx = ((size_t)t * p->n + k) * d_u + d;
-                sample[idx] = du_in[idx] * mean_scale + sd * orc_noise(pp, it, i, j, k, t * d_u + d);
+                sample[idx] = sample_entry(pp, it, i, j, k, t * d_u + d, du_in[idx], mean_scale, sd);
             }
 }
 
@@ -401,19 +407,26 @@ void orc_sample_fitness(const orc_problem *p, const orc_params *pp, int it, int 
     const size_t nu = (size_t)p->T * p->n * d_u;
     double *alpha = malloc(sizeof(double) * (pp->K + 1));
     double *abar = malloc(sizeof(double) * (pp->K + 1));
-    double *sample = malloc(sizeof(double) * nu);
-    double *ctrl = malloc(sizeof(double) * nu);
-    double *states = malloc(sizeof(double) * (size_t)(p->T + 1) * p->n * d_x);
     orc_schedule(pp->K, pp->beta0, pp->beta1, alpha, abar);
-    for (int c = 0; c < count; ++c) {
-        int j = js[c];
-        make_sample(p, pp, it, i, j, abar, du_in, sample);
-        for (size_t e = 0; e < nu; ++e) ctrl[e] = u_base[e] + sample[e];
-        orc_rollout(p, ctrl, states);
-        fitness[c] = orc_reward(p, pp->w_safe, states, gap ? &gap[c] : NULL);
-        if (fragile) fragile[c] = orc_fragile(p, states, delta);
+    /* samples are independent: each thread rolls out its own ones into
+     * private buffers and writes only their own output entries */
+#pragma omp parallel
+    {
+        double *sample = malloc(sizeof(double) * nu);
+        double *ctrl = malloc(sizeof(double) * nu);
+        double *states = malloc(sizeof(double) * (size_t)(p->T + 1) * p->n * d_x);
+#pragma omp for schedule(dynamic, 4)
+        for (int c = 0; c < count; ++c) {
+            int j = js[c];
+            make_sample(p, pp, it, i, j, abar, du_in, sample);
+            for (size_t e = 0; e < nu; ++e) ctrl[e] = u_base[e] + sample[e];
+            orc_rollout(p, ctrl, states);
+            fitness[c] = orc_reward(p, pp->w_safe, states, gap ? &gap[c] : NULL);
+            if (fragile) fragile[c] = orc_fragile(p, states, delta);
+        }
+        free(sample); free(ctrl); free(states);
     }
-    free(alpha); free(abar); free(sample); free(ctrl); free(states);
+    free(alpha); free(abar);
 }
 
 /* Weighted mean and one-step denoise, Algorithm 1 / Eq. (12)-(13):
@@ -425,21 +438,37 @@ void orc_weighted_update(const orc_problem *p, const orc_params *pp, int it, int
 {
     int d_x, d_u, d_p;
     orc_dims(p->dyn, &d_x, &d_u, &d_p);
-    const size_t nu = (size_t)p->T * p->n * d_u;
     double *alpha = malloc(sizeof(double) * (pp->K + 1));
     double *abar = malloc(sizeof(double) * (pp->K + 1));
-    double *sample = malloc(sizeof(double) * nu);
-    double *acc = calloc(nu, sizeof(double));
     orc_schedule(pp->K, pp->beta0, pp->beta1, alpha, abar);
-    for (int j = 0; j < pp->N; ++j) {
-        make_sample(p, pp, it, i, j, abar, du_in, sample);
-        for (size_t e = 0; e < nu; ++e) acc[e] += w[j] * sample[e];
-    }
     double mean_scale, sd, g;
     step_scales(pp, abar, i, &mean_scale, &sd, &g);
-    for (size_t e = 0; e < nu; ++e) du_out[e] = g * acc[e];
-    free(alpha); free(abar); free(sample); free(acc);
+    /* every entry is summed over samples j = 0..N-1 in order; robots are
+     * independent, so threads split them (same sums for any thread count).
+     * Entry (t, k, d) of sample j is the same sample_entry as in make_sample. */
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int k = 0; k < p->n; ++k) {
+        for (int t = 0; t < p->T; ++t)
+            for (int d = 0; d < d_u; ++d) {
+                size_t idx = ((size_t)t * p->n + k) * d_u + d;
+                double acc = 0.0;
+                for (int j = 0; j < pp->N; ++j)
+                    acc += w[j] * sample_entry(pp, it, i, j, k, t * d_u + d, du_in[idx], mean_scale, sd);
+                du_out[idx] = g * acc;
+            }
+    }
+    free(alpha); free(abar);
 }
+
+/* Thread count of the parallel sample loops (OpenMP builds; 1 otherwise). */
+#ifdef _OPENMP
+#include <omp.h>
+void orc_set_threads(int n) { omp_set_num_threads(n > 0 ? n : 1); }
+int orc_max_threads(void) { return omp_get_max_threads(); }
+#else
+void orc_set_threads(int n) { (void)n; }
+int orc_max_threads(void) { return 1; }
+#endif
 
 /* One denoising step (Algorithm 1 body for step i, applied to the
  * deformation of Algorithm 2).  fitness (optional, [N]) receives the

@@ -117,6 +117,10 @@ void orc_denoise_step(const orc_problem *p, const orc_params *pp, int it, int i,
 void orc_weighted_update(const orc_problem *p, const orc_params *pp, int it, int i,
                          const double *du_in, const double *w, double *du_out);
 void orc_apply(const orc_problem *p, const double *u_base, const double *du0, double *u_new);
+/* Threads of the parallel sample loops (OpenMP builds only). */
+void orc_set_threads(int n);
+int orc_max_threads(void);
+
 int orc_solve(const orc_problem *p, const orc_params *pp, int max_iters, int stop_on_success,
               int start_step, const double *du_init, double *u_out, orc_verdict *verdicts,
               int *iters_run);
