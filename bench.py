@@ -8,8 +8,9 @@ i.e. N * K * iters sample rollouts per step / step time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
 
-Default workload: 8 unicycle robots on a 4 m circle with antipodal goals and
-+-0.3 m jitter, T = 100, N = 2048, 100 steps x 5 iterations.
+Default workload: 16 3D holonomic robots on Fibonacci points of a 4 m sphere
+with antipodal goals, T = 100, N = 8192, 100 steps x 5 iterations (the
+largest single-GPU configuration).
 Multi-GPU (torchrun): every rank solves its own replica (independent
 instances, weak scaling); value = all ranks' sample rollouts / max time.
 
@@ -45,7 +46,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="unicycle_n8",
+    ap.add_argument("--workload", default="holo3d_n16",
                     choices=sorted(scenarios.WORKLOADS) + ["mixed512", "warmstart", "mppi_compare", "sensitivity"])
     ap.add_argument("--teams", type=int, default=200, help="held-out teams for --workload warmstart")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -197,11 +198,14 @@ def job_throughput(units_per_rank: float, world: int, max_ms: float) -> float:
     return units_per_rank * world / (max_ms / 1e3)
 
 
-def cpu_oracle_rate(inst, budget_s: float = 15.0, n_sample: int | None = None) -> dict:
+def cpu_oracle_rate(inst, budget_s: float = 15.0, n_sample: int | None = None, threads: int = 1) -> dict:
     """The oracle, as it stands, on a bounded sample: one denoising step over
     the first n_sample samples (fitness of each, weights, weighted-mean
-    update), repeated until ~budget_s of CPU time; single thread."""
+    update), repeated until ~budget_s of wall time, on `threads` host
+    threads (the oracle's OpenMP loops over samples and robots)."""
     import oracle
+    oracle.set_threads(threads)
+    threads = min(threads, oracle.max_threads())
     op = oracle.Problem(n=inst.n, T=inst.T, dyn=inst.dyn, integ=inst.integ, dt=inst.dt, radius=inst.radius,
                         start=inst.start, goal=inst.goal, u_lo=inst.u_lo, u_hi=inst.u_hi,
                         eps_margin=inst.eps_margin, goal_tol=inst.goal_tol, v_max=inst.v_max,
@@ -228,9 +232,49 @@ def cpu_oracle_rate(inst, budget_s: float = 15.0, n_sample: int | None = None) -
         t_total += time.perf_counter() - t0
         done += n_sample
         reps += 1
-    return {"value": done / t_total, "unit": UNIT, "cores": 1, "kind": "oracle", "samples": done,
+    return {"value": done / t_total, "unit": UNIT, "cores": threads, "kind": "oracle", "samples": done,
             "sample": f"{reps} denoising step(s) of {n_sample} of the {inst.N} samples of {inst.name} "
-                      f"(fitness + weights + update, FP64, 1 thread), {t_total:.1f} s"}
+                      f"(fitness + weights + update, FP64, {threads} thread(s)), {t_total:.1f} s"}
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline_line(inst, budget_s: float = 12.0) -> dict:
+    """The oracle on every host core (the reported baseline) and on one."""
+    cores = host_cores()
+    full = cpu_oracle_rate(inst, budget_s=budget_s, threads=cores)
+    one = cpu_oracle_rate(inst, budget_s=budget_s / 2, threads=1)
+    full["one_thread"] = {"value": one["value"], "sample": one["sample"]}
+    return full
+
+
+def measure_fp32_peak(torch, g, reps: int = 10) -> dict:
+    """Measured FP32 peak: the library's FFMA-chain probe over 8 CTAs of 256
+    threads per SM (eight independent chains per thread), best of `reps`
+    event-timed launches."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    blocks, threads, iters = sms * 8, 256, 4096
+    out = torch.empty(blocks * threads, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        g.d4orm_fp32_fma_probe(out, blocks, threads, iters, stream=stream)
+    best = None
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.d4orm_fp32_fma_probe(out, blocks, threads, iters, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        best = ms if best is None else min(best, ms)
+    flops = blocks * threads * iters * 16
+    return {"tflops": flops / (best / 1e3) / 1e12, "launch_ms": best,
+            "how": f"{blocks} x {threads} threads x {iters} iterations x 8 independent FFMA chains, best of {reps}"}
 
 
 def run_reference(args):
@@ -240,11 +284,13 @@ def run_reference(args):
         return
     inst = f32_inst(scenarios.WORKLOADS[args.workload]())
     per_step_budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
-    probe = cpu_oracle_rate(inst, budget_s=0.0, n_sample=4)
+    cores = host_cores()
+    probe = cpu_oracle_rate(inst, budget_s=0.0, n_sample=4 * cores, threads=cores)
     n_sample = int(max(8, min(inst.N, per_step_budget * probe["value"])))
     rates = []
     for s in range(args.warmup + args.steps):
-        r = cpu_oracle_rate(inst, budget_s=1e-9, n_sample=n_sample)  # exactly one step of n_sample samples
+        # exactly one step of n_sample samples on every host core
+        r = cpu_oracle_rate(inst, budget_s=1e-9, n_sample=n_sample, threads=cores)
         if s >= args.warmup:
             rates.append(r["value"])
     value = float(np.mean(rates))
@@ -253,8 +299,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": inst.name, "samples_per_step": n_sample, "of_N": inst.N,
-                       "threads": 1},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                       "threads": r["cores"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                              "sample": f"one denoising step over {n_sample} of {inst.N} samples per bench step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -351,11 +397,13 @@ def run_batched(args, torch, g, world, rank):
         # the oracle on a bounded sample of the batch: one denoising step of
         # 2 s over the first samples of every 64th problem
         picks = insts[::64]
-        parts = [cpu_oracle_rate(i, budget_s=2.0) for i in picks]
+        cores = host_cores()
+        parts = [cpu_oracle_rate(i, budget_s=2.0, threads=cores) for i in picks]
         secs = sum(p_["samples"] / p_["value"] for p_ in parts)
-        cpu = {"value": sum(p_["samples"] for p_ in parts) / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": sum(p_["samples"] for p_ in parts) / secs, "unit": UNIT, "cores": parts[0]["cores"],
+               "kind": "oracle",
                "sample": f"{len(picks)} of the 512 problems (every 64th), one denoising step over their first "
-                         f"samples each, FP64, 1 thread, {secs:.1f} s"}
+                         f"samples each, FP64, {parts[0]['cores']} thread(s), {secs:.1f} s"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -469,9 +517,13 @@ def run_warmstart(args, torch, g, world, rank):
                    "start_step": 30, "max_iterations": 5, "goal_tol_m": 0.5},
         "plain_median_ms": a.get("median_ms_plain"), "speedup": a.get("speedup"),
         "median_reward_ratio": a.get("median_reward_ratio"), "judged_worse_rate": a.get("judged_worse_rate"),
-        "fallback_rate": a.get("fallback_rate"), "solved": {"plain": a["plain_solved"], "warm": a["warm_solved"],
-                                                           "both": a.get("both", 0)},
-        "n16": res["n16"], "batched": res["batched"], "clocks": clocks.summary(),
+        "fallback_rate": a.get("fallback_rate"),
+        "solved": {"plain": a["plain_solved"], "warm_after_judge": a["warm_solved"],
+                   "warm_raw": a["warm_raw_solved"]},
+        "timing": "median over every team; unsolved teams count at their budget time; a warm plan that fails or "
+                  "scores > 1 % worse than the plain plan falls back to it with both solves' time charged",
+        "n16": res["n16"], "n15_16": res["n15_16"], "by_size": res["by_size"], "batched": res["batched"],
+        "clocks": clocks.summary(),
         "training": meta,
     }
     if rank == 0:
@@ -578,6 +630,7 @@ def run_ours(args):
     csum = clocks.summary()
     peak = fp32_peak_tflops(props.multi_processor_count, 2070.0)
     achieved = flops / (k2_ms / 1e3) / 1e12
+    measured = measure_fp32_peak(torch, g)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -594,6 +647,8 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": NCU_TRAFFIC_BYTES.get((k2_name, inst.name)),
                      "kernel": k2_name, "peak_basis": "FP32 lanes x 2 x 2070 MHz (152 SMs x 128)",
+                     "peak_measured": measured["tflops"], "frac_of_measured": achieved / measured["tflops"],
+                     "peak_measured_how": measured["how"],
                      "flops_per_launch": flops, "launch_ms": k2_ms,
                      "timing": f"{GRAPH_REPS} launches replayed from one CUDA graph, events on the stream",
                      "eager_event_launch_ms": float(kms[:, 0].mean())},
@@ -602,7 +657,7 @@ def run_ours(args):
         "verdict": results[-1]["verdict"],
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_oracle_rate(inst, budget_s=15.0)
+        line["cpu_baseline"] = cpu_baseline_line(inst)
     if rank == 0:
         print(json.dumps(line), flush=True)
     prob.close()

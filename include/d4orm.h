@@ -189,6 +189,12 @@ d4orm_status d4orm_problem_set_rollout_kernel(d4orm_problem *problem, int kernel
  * samples on the current device; -1 on error. */
 int d4orm_problem_rollout_kernel(const d4orm_problem *problem, int n_samples);
 
+/* How many iteration graphs d4orm_solve has captured on this handle so far
+ * (a diagnostic: a timed solve whose iteration shapes were all seen twice
+ * before replays graphs and captures none); -1 for a null handle.  The
+ * paper has no counterpart. */
+long long d4orm_problem_graph_captures(const d4orm_problem *problem);
+
 /* Rollout of one plan (Sec. IV-C; Algorithm 1 final line, Algorithm 2
  * update): controls u_dev[T][n][d_u] are held to the control box and
  * integrated from S.  states_dev (nullable) receives float[T+1][n][d_x].
@@ -229,8 +235,8 @@ d4orm_status d4orm_sample_fitness(d4orm_problem *problem, const d4orm_params *pa
  * kernels; synchronises and writes the device time of each kernel, in ms,
  * to kernel_ms_host[4]: {rollout+fitness, softmax weights, weighted noise
  * sum, finalize}.  A ~200 us sleep kernel runs first so that the events
- * bracket device time, not host submission.  Results are identical to
- * d4orm_denoise_step. */
+ * bracket device time, not host submission.
+ * Results are identical to d4orm_denoise_step. */
 d4orm_status d4orm_denoise_step_timed(d4orm_problem *problem, const d4orm_params *params, int iter, int step_i,
                                       const float *u_base_dev, const float *du_in_dev, float *du_out_dev,
                                       float *fitness_dev, float *kernel_ms_host, void *stream);
@@ -251,9 +257,13 @@ d4orm_status d4orm_denoise_step_timed(d4orm_problem *problem, const d4orm_params
  *    scratch must fit in D4ORM_NOALLOC_SCRATCH_FLOATS floats (every problem
  *    create accepts does on GPUs with up to 152 SMs); beyond either the call
  *    returns D4ORM_ERR_UNSUPPORTED before launching anything.
- *  - The first call on each device does a one-time set-up with that device
- *    current (looks up the array's device address, reads the SM count, sets
- *    kernel attributes); make that first call before any stream capture.
+ *  - Each call looks up the array's device address with the calling
+ *    thread's device current (the host-side name of the array is only a
+ *    stand-in) and sets the problem's rollout-kernel attributes; the first
+ *    call on a device also reads its SM count.  A changed address (the
+ *    context was re-created, e.g. after cudaDeviceReset) renews that
+ *    cached set-up.  Make the first call on a device, and the first after
+ *    a reset, before any stream capture.
  *  - Every call on a device shares the one array, which keeps the last
  *    call's contents (nothing in it needs to start at zero: each call writes
  *    all it reads).  Calls whose GPU work overlaps -- on different streams or
@@ -410,6 +420,15 @@ d4orm_status d4orm_sample_noise(d4orm_problem *problem, const d4orm_params *para
  * Philox(ctr_dev[i][0..3], key = (key0, key1)) for i < count. */
 d4orm_status d4orm_philox4x32_10(const uint32_t *ctr_dev, uint32_t key0, uint32_t key1, int count,
                                  uint32_t *out_dev, void *stream);
+
+/* Measured FP32 peak, the denominator the rollout kernel's FP32 fraction is
+ * also quoted against (the paper has no counterpart: this is a roofline
+ * instrument).  Launches `blocks` x `threads` threads, each running eight
+ * independent chains of `iters` fused multiply-adds, i.e.
+ * blocks * threads * iters * 16 FLOPs; time it with events on `stream`.
+ * out_dev (device, caller-owned) receives blocks * threads floats.
+ * threads must be a multiple of 32 in 32..1024; asynchronous. */
+d4orm_status d4orm_fp32_fma_probe(float *out_dev, int blocks, int threads, int iters, void *stream);
 
 /* Static string for a status code. */
 const char *d4orm_status_string(d4orm_status status);

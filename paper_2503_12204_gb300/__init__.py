@@ -37,9 +37,10 @@ STATUS = {0: "D4ORM_OK", 1: "D4ORM_ERR_INVALID_ARG", 2: "D4ORM_ERR_UNSUPPORTED",
 # Every entry point declared in include/d4orm.h.
 EXPORTS = (
     "d4orm_problem_create", "d4orm_problem_destroy", "d4orm_problem_set_rollout_kernel",
-    "d4orm_problem_rollout_kernel", "d4orm_rollout", "d4orm_sample_fitness", "d4orm_denoise_step",
+    "d4orm_problem_rollout_kernel", "d4orm_problem_graph_captures", "d4orm_rollout", "d4orm_sample_fitness",
+    "d4orm_denoise_step",
     "d4orm_denoise_step_timed", "d4orm_denoise_step_noalloc", "d4orm_solve",
-    "d4orm_sample_noise", "d4orm_philox4x32_10", "d4orm_status_string", "d4orm_last_error",
+    "d4orm_sample_noise", "d4orm_philox4x32_10", "d4orm_fp32_fma_probe", "d4orm_status_string", "d4orm_last_error",
     "d4orm_batch_create", "d4orm_batch_solve", "d4orm_batch_info", "d4orm_batch_destroy", "d4orm_solve_batched",
     "d4orm_warmstart_create", "d4orm_warmstart_destroy", "d4orm_warmstart_param_count",
     "d4orm_warmstart_get_params", "d4orm_warmstart_set_params", "d4orm_warmstart_forward",
@@ -137,8 +138,12 @@ def _load() -> ctypes.CDLL:
     lib.d4orm_solve.restype = i
     lib.d4orm_sample_noise.argtypes = [vp, ctypes.POINTER(_Params), i, i, i, i, vp, vp]
     lib.d4orm_sample_noise.restype = i
+    lib.d4orm_problem_graph_captures.argtypes = [vp]
+    lib.d4orm_problem_graph_captures.restype = ctypes.c_longlong
     lib.d4orm_philox4x32_10.argtypes = [vp, u32, u32, i, vp, vp]
     lib.d4orm_philox4x32_10.restype = i
+    lib.d4orm_fp32_fma_probe.argtypes = [vp, i, i, i, vp]
+    lib.d4orm_fp32_fma_probe.restype = i
     PP = ctypes.POINTER(vp)
     lib.d4orm_batch_create.argtypes = [PP, i, ctypes.POINTER(_Params), i, ctypes.POINTER(vp)]
     lib.d4orm_batch_create.restype = i
@@ -348,9 +353,19 @@ def d4orm_sample_noise(handle, params: Params, iter: int, step_i: int, j0: int, 
                                   _stream(stream)))
 
 
+def d4orm_problem_graph_captures(handle) -> int:
+    """Iteration graphs captured on this handle so far."""
+    return int(lib.d4orm_problem_graph_captures(handle))
+
+
 def d4orm_philox4x32_10(ctr_dev, key0: int, key1: int, count: int, out_dev, stream=None) -> None:
     _check(lib.d4orm_philox4x32_10(_ptr(ctr_dev), key0 & 0xFFFFFFFF, key1 & 0xFFFFFFFF, count, _ptr(out_dev),
                                    _stream(stream)))
+
+
+def d4orm_fp32_fma_probe(out_dev, blocks: int, threads: int, iters: int, stream=None) -> None:
+    """blocks * threads * iters * 16 FP32 FLOPs of independent FFMA chains."""
+    _check(lib.d4orm_fp32_fma_probe(_ptr(out_dev), blocks, threads, iters, _stream(stream)))
 
 
 def _ptr_array(items):

@@ -93,6 +93,7 @@ struct d4orm_problem {
     // graph cache (keyed by the parameters baked into the captured steps)
     d4orm_params g_params{};
     std::vector<GraphEntry> graphs;
+    long long graph_captures = 0;  // iteration graphs captured so far (diagnostic)
 };
 
 namespace {
@@ -340,6 +341,7 @@ d4orm_status iteration_graph(d4orm_problem* P, const d4orm_params* p, const std:
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     entry->exec = exec;
+    ++P->graph_captures;
     *out = exec;
     return D4ORM_OK;
 }
@@ -496,6 +498,8 @@ d4orm_status d4orm_problem_set_rollout_kernel(d4orm_problem* P, int kernel)
     }
     return D4ORM_OK;
 }
+
+long long d4orm_problem_graph_captures(const d4orm_problem* P) { return P ? P->graph_captures : -1; }
 
 int d4orm_problem_rollout_kernel(const d4orm_problem* P, int n_samples)
 {
@@ -717,6 +721,15 @@ d4orm_status d4orm_philox4x32_10(const uint32_t* ctr_dev, uint32_t key0, uint32_
     if (((uintptr_t)ctr_dev & 15) || ((uintptr_t)out_dev & 15))
         return fail(D4ORM_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
     D4_CUDA(launch_philox(ctr_dev, key0, key1, count, out_dev, (cudaStream_t)stream));
+    return D4ORM_OK;
+}
+
+d4orm_status d4orm_fp32_fma_probe(float* out_dev, int blocks, int threads, int iters, void* stream)
+{
+    if (!out_dev) return fail(D4ORM_ERR_INVALID_ARG, "out_dev is null");
+    if (blocks < 1 || threads < 32 || threads > 1024 || (threads & 31) || iters < 1)
+        return fail(D4ORM_ERR_INVALID_ARG, "blocks >= 1, threads a multiple of 32 in 32..1024, iters >= 1");
+    D4_CUDA(launch_fp32_fma_probe(out_dev, blocks, threads, iters, (cudaStream_t)stream));
     return D4ORM_OK;
 }
 

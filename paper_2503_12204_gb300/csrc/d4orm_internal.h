@@ -63,6 +63,7 @@ cudaError_t launch_sample_noise(const DevProblem& P, const DevStep& S, int j0, i
                                 cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t key0, uint32_t key1, int count, uint32_t* out,
                           cudaStream_t st);
+cudaError_t launch_fp32_fma_probe(float* out, int blocks, int threads, int iters, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // K5: batched persistent solver (k_batched.cu)

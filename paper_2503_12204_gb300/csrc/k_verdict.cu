@@ -88,6 +88,32 @@ __global__ void k_hold(int iterations)
     for (int i = 0; i < iterations; ++i) __nanosleep(1000);
 }
 
+// FP32 throughput probe: eight independent FFMA chains per thread
+// (a = a * b + c), so the FMA pipe, not latency, limits the rate when the
+// grid fills every SM.  One launch performs blocks * threads * iters * 8
+// FFMA (16 FLOPs per thread and iteration).  b and c come from the host so
+// the chains cannot be folded; the sums are stored so they cannot be dropped.
+__global__ void k_fp32_fma_probe(float* __restrict__ out, int iters, float b, float c)
+{
+    float a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = (float)(threadIdx.x + i) * 1e-3f;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = fmaf(a[i], b, c);
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += a[i];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+cudaError_t launch_fp32_fma_probe(float* out, int blocks, int threads, int iters, cudaStream_t st)
+{
+    k_fp32_fma_probe<<<blocks, threads, 0, st>>>(out, iters, 0.9999f, 1e-4f);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_hold(int microseconds, cudaStream_t st)
 {
     k_hold<<<1, 32, 0, st>>>(microseconds);
