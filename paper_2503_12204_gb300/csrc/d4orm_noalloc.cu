@@ -38,31 +38,24 @@ std::mutex g_setup_mu;
 
 size_t pad64(size_t n) { return (n + 63) / 64 * 64; }  // 256-byte slices
 
-// Once per device, with that device current: the array's device address
-// (the host-side name is only a stand-in), the SM count, and the dynamic
-// shared-memory opt-in of every rollout kernel variant.
+// Per device, with that device current: the array's device address (the
+// host-side name is only a stand-in) and the SM count.  The address is
+// queried again on every call (a host-side lookup, no device work); if it
+// differs from the cached one -- the context was destroyed and re-created,
+// e.g. after cudaDeviceReset -- the cached set-up is replaced.  The first
+// call on a device, and the first call after such a reset, should come
+// before any stream capture.
 d4orm_status setup_device(int dev, DeviceSetup** out)
 {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return d4orm::set_cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
     std::lock_guard<std::mutex> lock(g_setup_mu);
     DeviceSetup& s = g_setup[dev];
-    if (!s.done) {
-        void* ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess) return d4orm::set_cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    if (!s.done || s.scratch != static_cast<float*>(ptr)) {
         int sms = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return d4orm::set_cuda_error(e, "cudaDeviceGetAttribute");
-        d4orm::DevProblem probe{};
-        const int widths[] = {1, 2, 4, 8, 16, 32};
-        for (int obs = 0; obs <= 1; ++obs)
-            for (int dyn = d4orm::HOLO2D; dyn <= d4orm::DIFFDRIVE4; ++dyn)
-                for (int n : widths) {
-                    probe.dyn = dyn;
-                    probe.n = n;
-                    probe.n_obs = obs;
-                    e = d4orm::prepare_rollout_fitness(probe);
-                    if (e != cudaSuccess) return d4orm::set_cuda_error(e, "cudaFuncSetAttribute");
-                }
         s.scratch = static_cast<float*>(ptr);
         s.sm_count = sms;
         s.done = true;
@@ -94,6 +87,10 @@ extern "C" d4orm_status d4orm_denoise_step_noalloc(const d4orm_problem* problem,
     if (s != D4ORM_OK) return s;
 
     const DevProblem& P = dev_problem(problem);
+    // the dynamic shared-memory opt-in of this problem's rollout kernels (a
+    // kernel attribute of the current context: applied on every call, so a
+    // re-created context gets it too)
+    if ((e = prepare_rollout_fitness(P)) != cudaSuccess) return set_cuda_error(e, "cudaFuncSetAttribute");
     const SumSplit split = plan_weighted_sum(P, N, ds->sm_count);
     const size_t n_w = 2 * pad64((size_t)N), n_fit = pad64((size_t)N), n_stats = 64;
     const size_t n_partial = (size_t)split.chunks * P.n * P.Q * 4;
