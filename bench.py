@@ -88,8 +88,8 @@ def flops_per_sample_rollout(inst) -> int:
 # (summaries and commands in profiles/); a kernel changed since its capture
 # must be dropped from this table (its traffic is then reported as null).
 NCU_TRAFFIC_BYTES = {
+    ("k_rollout_fitness_paired", "holo3d_n16_T100_N8192"): 87296,
     ("k_rollout_fitness_pipe", "unicycle_n8_T100_N2048"): 38400,
-    ("k_rollout_fitness", "holo3d_n16_T100_N8192"): 88576,
     ("k_rollout_fitness", "unicycle_n8_T100_N2048"): 46080,
 }
 
@@ -625,7 +625,8 @@ def run_ours(args):
     share = (kms.mean(axis=0) / kms.mean(axis=0).sum()).tolist()
     flops = flops_per_sample_rollout(inst) * inst.N
     k2_kind = g.d4orm_problem_rollout_kernel(prob.handle, inst.N)
-    k2_name = {g.ROLLOUT_REGISTER: "k_rollout_fitness", g.ROLLOUT_PIPELINE: "k_rollout_fitness_pipe"}.get(k2_kind, "?")
+    k2_name = {g.ROLLOUT_REGISTER: "k_rollout_fitness", g.ROLLOUT_PIPELINE: "k_rollout_fitness_pipe",
+               g.ROLLOUT_PAIRED: "k_rollout_fitness_paired"}.get(k2_kind, "?")
     props = torch.cuda.get_device_properties(0)
     csum = clocks.summary()
     peak = fp32_peak_tflops(props.multi_processor_count, 2070.0)

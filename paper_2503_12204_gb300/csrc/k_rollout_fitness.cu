@@ -81,7 +81,9 @@ static cudaError_t prepare_k2_variant(const DevProblem& P)
 
 cudaError_t prepare_rollout_fitness(const DevProblem& P)
 {
-    const cudaError_t e = prepare_rollout_fitness_pipe(P);
+    cudaError_t e = prepare_rollout_fitness_pipe(P);
+    if (e != cudaSuccess) return e;
+    e = prepare_rollout_fitness_paired(P);
     if (e != cudaSuccess) return e;
     return P.n_obs > 0 ? prepare_k2_variant<true>(P) : prepare_k2_variant<false>(P);
 }
@@ -146,23 +148,33 @@ static cudaError_t dispatch_dyn(const DevProblem& P, const DevStep& S, const flo
 int resolve_rollout_kernel(const DevProblem& P, int N, int sm_count, int requested)
 {
     const bool pipe_fits = rollout_fitness_pipe_smem(P) <= 200 * 1024;
+    if (requested == D4ORM_ROLLOUT_PAIRED) return D4ORM_ROLLOUT_PAIRED;
     if (requested == D4ORM_ROLLOUT_PIPELINE && pipe_fits) return D4ORM_ROLLOUT_PIPELINE;
-    if (requested == D4ORM_ROLLOUT_REGISTER || !pipe_fits) return D4ORM_ROLLOUT_REGISTER;
-    // automatic: below about 2.5 warps per SM the register kernel leaves
-    // the SMs too idle and the pipelined kernel's parallelism along time
-    // wins (measured whole solves on GB300: unicycle, 8 robots, N = 1024 /
-    // 1.7 warps per SM: pipelined 12.6 vs register 13.4 ms; N = 2048 / 3.4
-    // warps per SM: register 14.3 vs pipelined 16.7 ms)
+    if (requested == D4ORM_ROLLOUT_REGISTER) return D4ORM_ROLLOUT_REGISTER;
     const int seg = P.n <= 1 ? 1 : P.n <= 2 ? 2 : P.n <= 4 ? 4 : P.n <= 8 ? 8 : P.n <= 16 ? 16 : 32;
     const long long warps = ((long long)N * seg + 31) / 32;
+    // automatic: with at least 3 warps per scheduler left after halving the
+    // warps, two robots per lane win (measured on GB300, 16 3D robots,
+    // N = 8192: 2048 paired warps 94.6 us vs 4096 register warps 100.5 us;
+    // the packed arithmetic needs fewer issue slots per robot-step)
+    const long long paired_warps = ((long long)N * paired_lanes(P.n) + 31) / 32;
+    if (P.n >= 2 && paired_warps >= 12LL * sm_count) return D4ORM_ROLLOUT_PAIRED;
+    if (!pipe_fits) return D4ORM_ROLLOUT_REGISTER;
+    // below about 2.5 warps per SM the register kernel leaves the SMs too
+    // idle and the pipelined kernel's parallelism along time wins (measured
+    // whole solves on GB300: unicycle, 8 robots, N = 1024 / 1.7 warps per
+    // SM: pipelined 12.6 vs register 13.4 ms; N = 2048 / 3.4 warps per SM:
+    // register 14.3 vs pipelined 16.7 ms)
     return 2 * warps < 5LL * sm_count ? D4ORM_ROLLOUT_PIPELINE : D4ORM_ROLLOUT_REGISTER;
 }
 
 cudaError_t launch_rollout_fitness(const DevProblem& P, const DevStep& S, const float* u_base, const float* du_in,
                                    float* fitness, const int* it_dev, int sm_count, int kernel, cudaStream_t st)
 {
-    if (resolve_rollout_kernel(P, S.N, sm_count, kernel) == D4ORM_ROLLOUT_PIPELINE)
-        return launch_rollout_fitness_pipe(P, S, u_base, du_in, fitness, it_dev, st);
+    const int kind = resolve_rollout_kernel(P, S.N, sm_count, kernel);
+    if (kind == D4ORM_ROLLOUT_PIPELINE) return launch_rollout_fitness_pipe(P, S, u_base, du_in, fitness, it_dev, st);
+    if (kind == D4ORM_ROLLOUT_PAIRED)
+        return launch_rollout_fitness_paired(P, S, u_base, du_in, fitness, it_dev, sm_count, st);
     return P.n_obs > 0 ? dispatch_dyn<true>(P, S, u_base, du_in, fitness, it_dev, sm_count, st)
                        : dispatch_dyn<false>(P, S, u_base, du_in, fitness, it_dev, sm_count, st);
 }

@@ -179,7 +179,7 @@ STEP_CASES = [
 ]
 
 
-@pytest.mark.parametrize("kernel", [1, 2], ids=["register", "pipeline"])
+@pytest.mark.parametrize("kernel", [1, 2, 3], ids=["register", "pipeline", "paired"])
 @pytest.mark.parametrize("dyn,integ,n,T,N,it,i", STEP_CASES)
 def test_denoise_step_parity(torch, g, oracle_lib, dyn, integ, n, T, N, it, i, kernel):
     inst = small_instance(dyn, n, T, N, integ=integ, seed=7, K=20)
@@ -197,7 +197,7 @@ OBSTACLE_CASES = [
 ]
 
 
-@pytest.mark.parametrize("kernel", [1, 2], ids=["register", "pipeline"])
+@pytest.mark.parametrize("kernel", [1, 2, 3], ids=["register", "pipeline", "paired"])
 @pytest.mark.parametrize("dyn,integ,n,T,N,m,reach", OBSTACLE_CASES)
 def test_denoise_step_parity_obstacles(torch, g, oracle_lib, dyn, integ, n, T, N, m, reach, kernel):
     """Appendix obstacle term inside the fused rollout + fitness: the same
@@ -264,7 +264,7 @@ MPPI_CASES = [
 ]
 
 
-@pytest.mark.parametrize("kernel", [1, 2], ids=["register", "pipeline"])
+@pytest.mark.parametrize("kernel", [1, 2, 3], ids=["register", "pipeline", "paired"])
 @pytest.mark.parametrize("dyn,integ,n,T,N,it,i,sigma", MPPI_CASES)
 def test_mppi_step_parity(torch, g, oracle_lib, dyn, integ, n, T, N, it, i, sigma, kernel):
     """The MPPI update rule on the same kernels: constant sigma around the
@@ -317,7 +317,7 @@ def test_mppi_solve_verdict_parity(torch, g, oracle_lib):
     assert abs(res["verdict"]["reward"] - verdicts[-1]["reward"]) < 0.05
 
 
-@pytest.mark.parametrize("kernel", [1, 2], ids=["register", "pipeline"])
+@pytest.mark.parametrize("kernel", [1, 2, 3], ids=["register", "pipeline", "paired"])
 @pytest.mark.parametrize("dyn,n,T,N", [(0, 5, 23, 300), (2, 8, 40, 257), (1, 3, 17, 64)])
 def test_sample_fitness_entry_point(torch, g, oracle_lib, dyn, n, T, N, kernel):
     """d4orm_sample_fitness writes exactly the fitness the full step writes,
@@ -346,8 +346,9 @@ def test_sample_fitness_entry_point(torch, g, oracle_lib, dyn, n, T, N, kernel):
 
 @pytest.mark.parametrize("dyn,n,T,N", [(0, 4, 50, 256), (2, 8, 100, 700), (1, 16, 37, 300), (3, 32, 9, 40)])
 def test_rollout_kernels_agree(torch, g, dyn, n, T, N):
-    """The register and pipeline kernels evaluate the same samples with the
-    same arithmetic; only the order of the fitness summation differs."""
+    """The register, pipeline and paired kernels evaluate the same samples
+    with the same arithmetic; only the order of the fitness summation
+    differs."""
     inst = small_instance(dyn, n, T, N, seed=13, K=20)
     rng = np.random.default_rng(2)
     ub = dev(torch, scenarios.random_controls(rng, inst, 0.5))
@@ -355,14 +356,15 @@ def test_rollout_kernels_agree(torch, g, dyn, n, T, N):
     prob = g.Problem(inst)
     p = gpu_params(g, inst)
     fits = []
-    for kernel in (1, 2):
+    for kernel in (1, 2, 3):
         g.d4orm_problem_set_rollout_kernel(prob.handle, kernel)
         f = torch.zeros(N, device="cuda")
         o = torch.zeros_like(du)
         g.d4orm_denoise_step(prob.handle, p, 2, 9, ub, du, o, f)
         fits.append(host(f))
     torch.cuda.synchronize()
-    assert np.abs(fits[0] - fits[1]).max() <= 2e-6 * max(1.0, np.abs(fits[0]).max())
+    for f in fits[1:]:
+        assert np.abs(fits[0] - f).max() <= 2e-6 * max(1.0, np.abs(fits[0]).max())
 
 
 def test_denoise_step_own_fitness_when_robust(torch, g, oracle_lib):
@@ -398,7 +400,19 @@ def test_denoise_step_at_the_control_size_limit(torch, g, oracle_lib):
     assert r["checked"] == 12
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+def test_auto_rollout_kernel_choice(torch, g):
+    """AUTO: two robots per lane for the 16-robot 3D workload (2048 paired
+    warps, above 3 per scheduler), one robot per lane for the 8-robot
+    unicycle workload, the pipelined kernel for the 4-robot workload."""
+    expect = {"holo3d_n16": g.ROLLOUT_PAIRED, "unicycle_n8": g.ROLLOUT_REGISTER, "holo2d_n4": g.ROLLOUT_PIPELINE}
+    for name, kind in expect.items():
+        inst = round_instance(scenarios.WORKLOADS[name]())
+        prob = g.Problem(inst)
+        if torch.cuda.get_device_properties(0).multi_processor_count == 152:
+            assert g.d4orm_problem_rollout_kernel(prob.handle, inst.N) == kind, name
+
+
+@pytest.mark.parametrize("kernel", [1, 2, 3])
 def test_denoise_step_is_deterministic(torch, g, kernel):
     inst = small_instance(1, 9, 40, 1000, seed=5)
     prob = g.Problem(inst)
