@@ -147,11 +147,17 @@ typedef struct {
 
 typedef struct {
     d4orm_verdict verdict;      /* of the returned plan                       */
-    int iters_run;
+    int iters_run;              /* completed iterations                       */
     int first_success_iter;     /* -1 if none                                 */
     double ms_to_success;       /* host wall clock from call entry; -1 if none*/
     double ms_total;            /* host wall clock of the whole call          */
+    int stop_reason;            /* D4ORM_STOP_BUDGET (max_iters or success),
+                                   D4ORM_STOP_DEADLINE or D4ORM_STOP_CANCELLED */
 } d4orm_result;
+
+#define D4ORM_STOP_BUDGET 0
+#define D4ORM_STOP_DEADLINE 1
+#define D4ORM_STOP_CANCELLED 2
 
 /* Create a problem (Sec. III).  Copies every host array; allocates no
  * device memory (device workspace is allocated on first compute call).
@@ -168,25 +174,30 @@ void d4orm_problem_destroy(d4orm_problem *problem);
 /* Rollout + fitness kernel used by the denoising steps of a problem.
  * REGISTER: one warp holds 32/SEG samples (SEG = next power of two >= n),
  * robots in lanes, state in registers over the whole horizon, pair terms by
- * shuffles.  PIPELINE: one rollout warp per 32/SEG samples plus helper warps
- * that generate the noise of the next time chunk and score the previous one
- * (for batches too small to fill the GPU with the register kernel).  AUTO
- * picks PIPELINE when the register kernel would have fewer than 2.5 warps
- * per SM, else REGISTER (the pipelined kernel also needs its shared memory
- * to fit in 200 KB).  Both compute the same fitness (summation order
+ * shuffles.  PAIRED: the same with two robots per lane (32/(SEG/2) samples
+ * per warp), the two robots' state sharing 64-bit registers so that their
+ * arithmetic issues as packed f32x2 instructions.  PIPELINE: one rollout
+ * warp per 32/SEG samples plus helper warps that generate the noise of the
+ * next time chunk and score the previous one (for batches too small to
+ * fill the GPU with the register kernel).  AUTO picks PIPELINE when the
+ * register kernel would have fewer than 2.5 warps per SM, PAIRED when the
+ * paired kernel still has at least 3 warps per scheduler (12 per SM) and
+ * n >= 2, else REGISTER (the pipelined kernel also needs its shared memory
+ * to fit in 200 KB).  All compute the same fitness (summation order
  * aside). */
 typedef enum {
     D4ORM_ROLLOUT_AUTO = 0,
     D4ORM_ROLLOUT_REGISTER = 1,
-    D4ORM_ROLLOUT_PIPELINE = 2
+    D4ORM_ROLLOUT_PIPELINE = 2,
+    D4ORM_ROLLOUT_PAIRED = 3
 } d4orm_rollout_kernel;
 
 /* Choose the rollout kernel of a problem (default AUTO).  Host only.
  * Errors: INVALID_ARG for a null problem or an unknown kind. */
 d4orm_status d4orm_problem_set_rollout_kernel(d4orm_problem *problem, int kernel);
 
-/* The kernel (REGISTER or PIPELINE) the problem's steps use for n_samples
- * samples on the current device; -1 on error. */
+/* The kernel (REGISTER, PIPELINE or PAIRED) the problem's steps use for
+ * n_samples samples on the current device; -1 on error. */
 int d4orm_problem_rollout_kernel(const d4orm_problem *problem, int n_samples);
 
 /* How many iteration graphs d4orm_solve has captured on this handle so far
@@ -285,6 +296,15 @@ d4orm_status d4orm_denoise_step_noalloc(const d4orm_problem *problem, const d4or
 d4orm_status d4orm_solve(d4orm_problem *problem, const d4orm_params *params, const d4orm_budget *budget,
                          const float *du_init_dev, float *u_out_dev, d4orm_result *out_host, void *stream);
 
+/* Ask the running (or the next) d4orm_solve of this problem to stop before
+ * its next iteration: it returns D4ORM_ERR_CANCELLED with the plan of the
+ * iterations already completed (stop_reason D4ORM_STOP_CANCELLED).  The
+ * request is consumed by that solve.  A solve without stop_on_success and
+ * without a deadline enqueues its iterations without waiting for them, so
+ * a request arriving during it stops only the iterations not yet enqueued.
+ * Thread-safe.  The paper has no counterpart (a host control). */
+d4orm_status d4orm_problem_cancel(d4orm_problem *problem);
+
 /* ---------------------------------------------------------------------------
  * Batched persistent solve.  Many independent problems -- any mix of robot
  * counts, horizons and dynamics -- solved by Algorithm 2 in ONE persistent
@@ -315,15 +335,31 @@ d4orm_status d4orm_batch_create(d4orm_problem *const *problems, int count, const
  * nullable host array [count] of device pointers: warm-start deformations
  * entering the first iteration at budget->start_step.  out_host (nullable):
  * [count] results; ms_to_success / ms_total are device-clock times of each
- * problem's own solve (from when its CTA picked it up).  budget->deadline_ms
- * must be <= 0 (UNSUPPORTED otherwise).  Synchronises the device before
- * and `stream` after the launch. */
+ * problem's own solve (from when its CTA picked it up).
+ * Anytime stops (Sec. IV-D: the plan of the last completed iteration is
+ * always a valid answer), checked by every CTA before each denoising step:
+ *  - budget->deadline_ms > 0: device clock since the launch; a problem
+ *    whose deadline passes keeps the plan of its completed iterations
+ *    (stop_reason D4ORM_STOP_DEADLINE) and problems not yet started get
+ *    none (iters_run 0).
+ *  - d4orm_batch_cancel from any host thread (or before the call): the
+ *    same, with stop_reason D4ORM_STOP_CANCELLED.
+ * Returns D4ORM_ERR_CANCELLED if the solve was cancelled, D4ORM_ERR_TIMEOUT
+ * if the deadline left some problem without any completed iteration, else
+ * OK; plans and results are written in every case.  Synchronises the
+ * device before and `stream` after the launch. */
 d4orm_status d4orm_batch_solve(d4orm_batch *batch, const d4orm_budget *budget, const float *const *du_init_dev,
                                float *const *u_out_dev, d4orm_result *out_host, void *stream);
 
 /* Launch shape the batch uses and the autotuner's pilot times (ms, -1 when
  * a width was not tried) for 128 / 256 / 512 threads. */
 d4orm_status d4orm_batch_info(const d4orm_batch *batch, int *threads_per_cta, int *ctas, float *tuned_ms);
+
+/* Request that the running (or the next) d4orm_batch_solve of this batch
+ * stop at the next denoising-step boundary of every CTA.  Thread-safe; sets
+ * a flag in host memory mapped into the device, which the solve clears
+ * when it returns.  The paper has no counterpart (a host control). */
+d4orm_status d4orm_batch_cancel(d4orm_batch *batch);
 
 /* Free a batch (synchronises the device).  NULL is a no-op. */
 void d4orm_batch_destroy(d4orm_batch *batch);

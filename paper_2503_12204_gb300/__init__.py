@@ -21,7 +21,9 @@ LIB_PATH = os.path.join(_HERE, "libd4orm.so")
 
 HOLO2D, HOLO3D, UNICYCLE, DIFFDRIVE4 = 0, 1, 2, 3
 EULER, RK4 = 0, 1
-ROLLOUT_AUTO, ROLLOUT_REGISTER, ROLLOUT_PIPELINE = 0, 1, 2
+ROLLOUT_AUTO, ROLLOUT_REGISTER, ROLLOUT_PIPELINE, ROLLOUT_PAIRED = 0, 1, 2, 3
+STOP_BUDGET, STOP_DEADLINE, STOP_CANCELLED = 0, 1, 2
+ERR_TIMEOUT, ERR_CANCELLED = 5, 6
 UPDATE_DENOISE, UPDATE_MPPI = 0, 1
 DIMS = {HOLO2D: (4, 2, 2), HOLO3D: (6, 3, 3), UNICYCLE: (3, 2, 2), DIFFDRIVE4: (4, 2, 2)}
 MAX_ROBOTS = 32
@@ -39,9 +41,10 @@ EXPORTS = (
     "d4orm_problem_create", "d4orm_problem_destroy", "d4orm_problem_set_rollout_kernel",
     "d4orm_problem_rollout_kernel", "d4orm_problem_graph_captures", "d4orm_rollout", "d4orm_sample_fitness",
     "d4orm_denoise_step",
-    "d4orm_denoise_step_timed", "d4orm_denoise_step_noalloc", "d4orm_solve",
+    "d4orm_denoise_step_timed", "d4orm_denoise_step_noalloc", "d4orm_solve", "d4orm_problem_cancel",
     "d4orm_sample_noise", "d4orm_philox4x32_10", "d4orm_fp32_fma_probe", "d4orm_status_string", "d4orm_last_error",
-    "d4orm_batch_create", "d4orm_batch_solve", "d4orm_batch_info", "d4orm_batch_destroy", "d4orm_solve_batched",
+    "d4orm_batch_create", "d4orm_batch_solve", "d4orm_batch_info", "d4orm_batch_cancel", "d4orm_batch_destroy",
+    "d4orm_solve_batched",
     "d4orm_warmstart_create", "d4orm_warmstart_destroy", "d4orm_warmstart_param_count",
     "d4orm_warmstart_get_params", "d4orm_warmstart_set_params", "d4orm_warmstart_forward",
     "d4orm_warmstart_loss_grad", "d4orm_warmstart_train_step", "d4orm_warmstart_features",
@@ -52,9 +55,13 @@ BATCH_MAX_SAMPLES = 8192
 
 
 class D4ormError(RuntimeError):
-    def __init__(self, status: int, message: str):
+    """A non-OK status.  For D4ORM_ERR_CANCELLED and D4ORM_ERR_TIMEOUT of a
+    solve, `results` holds what the call wrote (the anytime plans' results)."""
+
+    def __init__(self, status: int, message: str, results=None):
         super().__init__(f"{STATUS.get(status, status)}: {message}")
         self.status = status
+        self.results = results
 
 
 class _Desc(ctypes.Structure):
@@ -103,7 +110,7 @@ class _Verdict(ctypes.Structure):
 class _Result(ctypes.Structure):
     _fields_ = [
         ("verdict", _Verdict), ("iters_run", ctypes.c_int), ("first_success_iter", ctypes.c_int),
-        ("ms_to_success", ctypes.c_double), ("ms_total", ctypes.c_double),
+        ("ms_to_success", ctypes.c_double), ("ms_total", ctypes.c_double), ("stop_reason", ctypes.c_int),
     ]
 
 
@@ -151,6 +158,10 @@ def _load() -> ctypes.CDLL:
     lib.d4orm_batch_solve.restype = i
     lib.d4orm_batch_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_float)]
     lib.d4orm_batch_info.restype = i
+    lib.d4orm_batch_cancel.argtypes = [vp]
+    lib.d4orm_batch_cancel.restype = i
+    lib.d4orm_problem_cancel.argtypes = [vp]
+    lib.d4orm_problem_cancel.restype = i
     lib.d4orm_batch_destroy.argtypes = [vp]
     lib.d4orm_batch_destroy.restype = None
     lib.d4orm_solve_batched.argtypes = [PP, i, ctypes.POINTER(_Params), ctypes.POINTER(_Budget), PP,
@@ -337,13 +348,36 @@ def d4orm_denoise_step_noalloc(handle, params: Params, iter: int, step_i: int, u
                                           _ptr(du_in_dev), _ptr(du_out_dev), _ptr(fitness_dev), _stream(stream)))
 
 
+def _anytime_check(status: int, results) -> None:
+    """Raise for a non-OK status; a cancelled or timed-out solve carries the
+    results it wrote."""
+    if status in (ERR_TIMEOUT, ERR_CANCELLED):
+        raise D4ormError(status, lib.d4orm_last_error().decode(errors="replace"), results)
+    _check(status)
+
+
+def _result(r) -> dict:
+    return dict(verdict=_verdict(r.verdict), iters_run=r.iters_run, first_success_iter=r.first_success_iter,
+                ms_to_success=r.ms_to_success, ms_total=r.ms_total, stop_reason=r.stop_reason)
+
+
 def d4orm_solve(handle, params: Params, budget: Budget, u_out_dev, du_init_dev=None, stream=None) -> dict:
     pc, bc = params.c(), budget.c()
     r = _Result()
-    _check(lib.d4orm_solve(handle, ctypes.byref(pc), ctypes.byref(bc), _ptr(du_init_dev), _ptr(u_out_dev),
-                           ctypes.byref(r), _stream(stream)))
-    return dict(verdict=_verdict(r.verdict), iters_run=r.iters_run, first_success_iter=r.first_success_iter,
-                ms_to_success=r.ms_to_success, ms_total=r.ms_total)
+    status = lib.d4orm_solve(handle, ctypes.byref(pc), ctypes.byref(bc), _ptr(du_init_dev), _ptr(u_out_dev),
+                             ctypes.byref(r), _stream(stream))
+    _anytime_check(status, _result(r))
+    return _result(r)
+
+
+def d4orm_problem_cancel(handle) -> None:
+    """Stop the running (or next) solve of this problem before its next iteration."""
+    _check(lib.d4orm_problem_cancel(handle))
+
+
+def d4orm_batch_cancel(batch) -> None:
+    """Stop the running (or next) batched solve at every CTA's next step."""
+    _check(lib.d4orm_batch_cancel(batch))
 
 
 def d4orm_sample_noise(handle, params: Params, iter: int, step_i: int, j0: int, count: int, eps_dev,
@@ -377,8 +411,7 @@ def _ptr_array(items):
 
 
 def _results(res, count):
-    return [dict(verdict=_verdict(r.verdict), iters_run=r.iters_run, first_success_iter=r.first_success_iter,
-                 ms_to_success=r.ms_to_success, ms_total=r.ms_total) for r in list(res)[:count]]
+    return [_result(r) for r in list(res)[:count]]
 
 
 def d4orm_batch_create(handles, params: Params, autotune: bool = False) -> ctypes.c_void_p:
@@ -395,7 +428,8 @@ def d4orm_batch_solve(batch, budget: Budget, u_out_devs, du_init_devs=None, stre
     outs = _ptr_array(u_out_devs)
     inits = _ptr_array(du_init_devs) if du_init_devs is not None else None
     res = (_Result * len(u_out_devs))()
-    _check(lib.d4orm_batch_solve(batch, ctypes.byref(bc), inits, outs, res, _stream(stream)))
+    status = lib.d4orm_batch_solve(batch, ctypes.byref(bc), inits, outs, res, _stream(stream))
+    _anytime_check(status, _results(res, len(u_out_devs)))
     return _results(res, len(u_out_devs))
 
 

@@ -39,9 +39,13 @@ struct d4orm_batch {
     int threads = 256, grid = 0;
     bool obstacles = false;            // any problem has obstacles: the kernel variant with the penalty
     float tuned_ms[3] = {-1.f, -1.f, -1.f};
-    // cached graph for one (max_iters, stop_on_success, start_step, warm) combination
+    // cached graph for one (max_iters, stop_on_success, start_step, deadline) combination
     cudaGraphExec_t graph = nullptr;
     int g_iters = -1, g_stop = -1, g_start = -1;
+    long long g_deadline = -1;
+    // host-mapped cancel flag: written by d4orm_batch_cancel, read by the kernel
+    int* h_cancel = nullptr;
+    int* d_cancel = nullptr;
 };
 
 namespace {
@@ -58,6 +62,7 @@ void batch_free(d4orm_batch* B)
     cudaFree(B->d_work);
     cudaFreeHost(B->h_insts);
     cudaFreeHost(B->h_results);
+    cudaFreeHost(B->h_cancel);
 }
 
 #define B_CUDA(call)                                                     \
@@ -77,6 +82,8 @@ d4orm_status pilot_ms(d4orm_batch* B, int threads, float* ms)
     }
     const int grid = std::min(B->count, B->sms * occ);
     BatchConsts P = B->C;
+    P.deadline_ns = 0;
+    P.cancel = nullptr;
     P.K = std::min(2, B->C.K);
     P.max_iters = 1;
     P.stop_on_success = 0;
@@ -177,6 +184,11 @@ d4orm_status d4orm_batch_create(d4orm_problem* const* problems, int count, const
     if (e == cudaSuccess) e = cudaMalloc(&B->d_results, sizeof(BatchResult) * count);
     if (e == cudaSuccess) e = cudaMallocHost(&B->h_results, sizeof(BatchResult) * count);
     if (e == cudaSuccess) e = cudaMalloc(&B->d_work, sizeof(float) * 3 * total);
+    if (e == cudaSuccess) e = cudaHostAlloc(&B->h_cancel, sizeof(int), cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        *(volatile int*)B->h_cancel = 0;
+        e = cudaHostGetDevicePointer((void**)&B->d_cancel, B->h_cancel, 0);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail_cleanup(set_error(e == cudaErrorMemoryAllocation ? D4ORM_ERR_OOM : D4ORM_ERR_CUDA,
@@ -266,8 +278,6 @@ d4orm_status d4orm_batch_solve(d4orm_batch* B, const d4orm_budget* budget, const
     if (!B || !budget || !u_out_dev) return set_error(D4ORM_ERR_INVALID_ARG, "null batch, budget or u_out_dev");
     if (budget->max_iters < 1 || budget->max_iters > D4ORM_MAX_ITERS)
         return set_error(D4ORM_ERR_INVALID_ARG, "max_iters out of range");
-    if (budget->deadline_ms > 0.0)
-        return set_error(D4ORM_ERR_UNSUPPORTED, "batched solve: deadline_ms is not supported (use max_iters)");
     const bool warm = du_init_dev != nullptr;
     if (warm && (budget->start_step < 1 || budget->start_step > B->params.n_steps))
         return set_error(D4ORM_ERR_INVALID_ARG, "start_step out of 1..K");
@@ -284,8 +294,11 @@ d4orm_status d4orm_batch_solve(d4orm_batch* B, const d4orm_budget* budget, const
         B->h_insts[b].du_init = warm ? du_init_dev[b] : nullptr;
     }
     const int start = warm ? budget->start_step : 0;
+    // deadline on the device clock, at least 1 ns when one is set
+    const long long deadline_ns =
+        budget->deadline_ms > 0.0 ? std::max(1LL, (long long)std::llround(budget->deadline_ms * 1e6)) : 0;
     if (!B->graph || B->g_iters != budget->max_iters || B->g_stop != (budget->stop_on_success ? 1 : 0) ||
-        B->g_start != start) {
+        B->g_start != start || B->g_deadline != deadline_ns) {
         if (B->graph) {
             cudaGraphExecDestroy(B->graph);
             B->graph = nullptr;
@@ -294,6 +307,8 @@ d4orm_status d4orm_batch_solve(d4orm_batch* B, const d4orm_budget* budget, const
         C.max_iters = budget->max_iters;
         C.stop_on_success = budget->stop_on_success ? 1 : 0;
         C.start_step = warm ? budget->start_step : B->params.n_steps;
+        C.deadline_ns = deadline_ns;
+        C.cancel = B->d_cancel;
         cudaStream_t cap;
         B_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         cudaGraph_t g = nullptr;
@@ -319,10 +334,20 @@ d4orm_status d4orm_batch_solve(d4orm_batch* B, const d4orm_budget* budget, const
         B->g_iters = budget->max_iters;
         B->g_stop = budget->stop_on_success ? 1 : 0;
         B->g_start = start;
+        B->g_deadline = deadline_ns;
     }
     B_CUDA(cudaGraphLaunch(B->graph, st));
-    B_CUDA(cudaStreamSynchronize(st));
+    const cudaError_t sync = cudaStreamSynchronize(st);
+    // a cancel request covers this solve only
+    __atomic_store_n(B->h_cancel, 0, __ATOMIC_SEQ_CST);
+    if (sync != cudaSuccess) return set_cuda_error(sync, "cudaStreamSynchronize(batched solve)");
     const double wall = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    bool cancelled = false, starved = false;
+    for (int b = 0; b < B->count; ++b) {
+        const BatchResult& r = B->h_results[b];
+        cancelled = cancelled || r.stop_reason == D4ORM_STOP_CANCELLED;
+        starved = starved || (r.stop_reason == D4ORM_STOP_DEADLINE && r.iters_run == 0);
+    }
     if (out_host) {
         for (int b = 0; b < B->count; ++b) {
             const BatchResult& r = B->h_results[b];
@@ -332,9 +357,20 @@ d4orm_status d4orm_batch_solve(d4orm_batch* B, const d4orm_budget* budget, const
             o.first_success_iter = r.first_success_iter;
             o.ms_to_success = r.ns_to_success >= 0 ? r.ns_to_success * 1e-6 : -1.0;
             o.ms_total = r.ns_total * 1e-6;
+            o.stop_reason = r.stop_reason;
         }
     }
     (void)wall;
+    if (cancelled) return set_error(D4ORM_ERR_CANCELLED, "batched solve cancelled (plans of completed iterations kept)");
+    if (starved)
+        return set_error(D4ORM_ERR_TIMEOUT, "deadline passed before some problem completed an iteration");
+    return D4ORM_OK;
+}
+
+d4orm_status d4orm_batch_cancel(d4orm_batch* B)
+{
+    if (!B || !B->h_cancel) return set_error(D4ORM_ERR_INVALID_ARG, "null batch");
+    __atomic_store_n(B->h_cancel, 1, __ATOMIC_SEQ_CST);
     return D4ORM_OK;
 }
 

@@ -1,6 +1,7 @@
 // d4orm_capi.cu -- the extern "C" boundary (include/d4orm.h): argument
 // validation, the host-side FP64 noise schedule, per-handle device
 // workspace, and the Algorithm 2 solve loop replayed from CUDA graphs.
+#include <atomic>
 #include <chrono>
 #include <cstdarg>
 #include <cmath>
@@ -94,6 +95,7 @@ struct d4orm_problem {
     d4orm_params g_params{};
     std::vector<GraphEntry> graphs;
     long long graph_captures = 0;  // iteration graphs captured so far (diagnostic)
+    std::atomic<int> cancel{0};    // set by d4orm_problem_cancel, consumed by d4orm_solve
 };
 
 namespace {
@@ -490,7 +492,8 @@ void d4orm_problem_destroy(d4orm_problem* P)
 d4orm_status d4orm_problem_set_rollout_kernel(d4orm_problem* P, int kernel)
 {
     if (!P) return fail(D4ORM_ERR_INVALID_ARG, "null problem");
-    if (kernel != D4ORM_ROLLOUT_AUTO && kernel != D4ORM_ROLLOUT_REGISTER && kernel != D4ORM_ROLLOUT_PIPELINE)
+    if (kernel != D4ORM_ROLLOUT_AUTO && kernel != D4ORM_ROLLOUT_REGISTER && kernel != D4ORM_ROLLOUT_PIPELINE &&
+        kernel != D4ORM_ROLLOUT_PAIRED)
         return fail(D4ORM_ERR_INVALID_ARG, "unknown rollout kernel %d", kernel);
     if (kernel != P->rollout_kernel) {
         free_graphs(P);
@@ -597,6 +600,10 @@ d4orm_status d4orm_solve(d4orm_problem* P, const d4orm_params* params, const d4o
     res.ms_to_success = -1.0;
     int it = 0;
     for (; it < budget->max_iters; ++it) {
+        if (P->cancel.exchange(0)) {
+            res.stop_reason = D4ORM_STOP_CANCELLED;
+            break;
+        }
         const bool warm = (it == 0 && du_init_dev);
         const int i0 = warm ? budget->start_step : params->n_steps;
         if (warm)
@@ -633,6 +640,7 @@ d4orm_status d4orm_solve(d4orm_problem* P, const d4orm_params* params, const d4o
         }
         if (budget->deadline_ms > 0.0 && ms >= budget->deadline_ms) {
             ++it;
+            if (it < budget->max_iters) res.stop_reason = D4ORM_STOP_DEADLINE;
             break;
         }
     }
@@ -647,12 +655,21 @@ d4orm_status d4orm_solve(d4orm_problem* P, const d4orm_params* params, const d4o
             const d4orm_verdict v = P->h_verdicts[1 + i];
             if (res.first_success_iter < 0 && v.collision_free && v.goal_reached) res.first_success_iter = i;
         }
-        res.verdict = P->h_verdicts[n_it];
+        if (n_it > 0) res.verdict = P->h_verdicts[n_it];
     } else {
         D4_CUDA(cudaStreamSynchronize(st));
     }
     res.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     if (out_host) *out_host = res;
+    if (res.stop_reason == D4ORM_STOP_CANCELLED)
+        return fail(D4ORM_ERR_CANCELLED, "solve cancelled after %d iteration(s) (their plan is kept)", it);
+    return D4ORM_OK;
+}
+
+d4orm_status d4orm_problem_cancel(d4orm_problem* P)
+{
+    if (!P) return fail(D4ORM_ERR_INVALID_ARG, "null problem");
+    P->cancel.store(1);
     return D4ORM_OK;
 }
 

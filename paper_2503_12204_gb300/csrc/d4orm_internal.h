@@ -21,9 +21,9 @@ SumSplit plan_weighted_sum(const DevProblem& P, int N, int sm_count);
 cudaError_t prepare_rollout_fitness(const DevProblem& P);
 cudaError_t prepare_rollout_fitness_pipe(const DevProblem& P);
 
-// Which rollout kernel serves (P, N): D4ORM_ROLLOUT_REGISTER or
-// D4ORM_ROLLOUT_PIPELINE (requested AUTO picks by how full the register
-// kernel would keep the GPU).
+// Which rollout kernel serves (P, N): D4ORM_ROLLOUT_REGISTER,
+// D4ORM_ROLLOUT_PIPELINE or D4ORM_ROLLOUT_PAIRED (requested AUTO picks by
+// how full each would keep the GPU).
 int resolve_rollout_kernel(const DevProblem& P, int N, int sm_count, int requested);
 
 // K2: fused sample rollout + fitness (Eq. (12) samples, Eq. (1) rollout,
@@ -31,6 +31,12 @@ int resolve_rollout_kernel(const DevProblem& P, int N, int sm_count, int request
 cudaError_t launch_rollout_fitness(const DevProblem& P, const DevStep& S, const float* u_base,
                                    const float* du_in, float* fitness, const int* it_dev, int sm_count, int kernel,
                                    cudaStream_t st);
+// K2b: two robots per lane (same results up to summation order).
+cudaError_t prepare_rollout_fitness_paired(const DevProblem& P);
+cudaError_t launch_rollout_fitness_paired(const DevProblem& P, const DevStep& S, const float* u_base,
+                                          const float* du_in, float* fitness, const int* it_dev, int sm_count,
+                                          cudaStream_t st);
+int paired_lanes(int n);
 // K2p: the warp-specialised variant (same results up to summation order).
 cudaError_t launch_rollout_fitness_pipe(const DevProblem& P, const DevStep& S, const float* u_base,
                                         const float* du_in, float* fitness, const int* it_dev, cudaStream_t st);
@@ -84,6 +90,8 @@ struct BatchConsts {
     uint32_t rk0[10], rk1[10];
     uint32_t tag_base;
     float w_safe, inv_lambda;
+    long long deadline_ns;        // > 0: stop once the device clock passes launch + deadline
+    const volatile int* cancel;   // nullable: host-mapped flag, non-zero = stop
 };
 
 struct BatchResult {
@@ -92,6 +100,7 @@ struct BatchResult {
     int first_success_iter;
     long long ns_to_success;  // device clock from the instance's start; -1 if none
     long long ns_total;       // device clock of the instance's solve
+    int stop_reason;          // D4ORM_STOP_*
 };
 
 // `obstacles` selects the kernel variant with the obstacle penalty compiled

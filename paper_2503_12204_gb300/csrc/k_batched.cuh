@@ -32,7 +32,8 @@ template <int DYN, int SEG, bool OBS>
 __device__ __noinline__ void batched_instance(const DevProblem& P, const BatchInstance& I, const BatchConsts& C,
                                                  const float4* __restrict__ sched, int b, float* sM, float* sFit,
                                                  float2* sList, float4* sRed, float* sh, int* scan, int* s_count,
-                                                 d4orm_verdict* s_verdict, BatchResult* results)
+                                                 d4orm_verdict* s_verdict, BatchResult* results, long long t_launch,
+                                                 int* s_stop)
 {
     constexpr int DU = DynDims<DYN>::DU;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -44,10 +45,22 @@ __device__ __noinline__ void batched_instance(const DevProblem& P, const BatchIn
     const long long t_start = globaltimer_ns();
 
     for (int e = tid; e < nctrl; e += nt) tau[e] = 0.0f;
-    int first = -1, iters = 0;
+    int first = -1, iters = 0, stop = 0;
     long long t_success = -1;
     d4orm_verdict last{};
-    for (int it = 0; it < C.max_iters; ++it) {
+    // anytime stop (deadline or host cancel), decided by thread 0 before each
+    // step and shared through shared memory so the whole CTA leaves together
+    auto must_stop = [&]() {
+        if (tid == 0) {
+            int r = 0;
+            if (C.cancel && *C.cancel) r = D4ORM_STOP_CANCELLED;
+            else if (C.deadline_ns > 0 && globaltimer_ns() - t_launch > C.deadline_ns) r = D4ORM_STOP_DEADLINE;
+            *s_stop = r;
+        }
+        __syncthreads();
+        return *s_stop;
+    };
+    for (int it = 0; it < C.max_iters && !stop; ++it) {
         // dU_K = 0 (Sec. IV-D); a warm start enters the first iteration at
         // start_step with the given deformation
         const bool warm = (it == 0) && I.du_init != nullptr;
@@ -56,6 +69,7 @@ __device__ __noinline__ void batched_instance(const DevProblem& P, const BatchIn
         int cur = 0;
         const uint32_t c3 = (uint32_t)it | ((C.tag_base + (uint32_t)b) << 12);
         for (int i = warm ? C.start_step : C.K; i >= 1; --i) {
+            if ((stop = must_stop()) != 0) break;
             DevStep S;
 #pragma unroll
             for (int r = 0; r < 10; ++r) {
@@ -131,6 +145,7 @@ __device__ __noinline__ void batched_instance(const DevProblem& P, const BatchIn
             }
             cur ^= 1;
         }
+        if (stop) break;  // an interrupted iteration is discarded: tau.u keeps the completed ones
         // iteration end: tau.u <- clip(tau.u + dU_0), rollout, verdict
         if (warp == 0) apply_rollout_verdict_warp<DYN>(P, C.w_safe, tau, du[cur], tau, nullptr, s_verdict);
         __syncthreads();
@@ -151,6 +166,7 @@ __device__ __noinline__ void batched_instance(const DevProblem& P, const BatchIn
         r.first_success_iter = first;
         r.ns_to_success = t_success >= 0 ? t_success - t_start : -1;
         r.ns_total = globaltimer_ns() - t_start;
+        r.stop_reason = stop;
         results[b] = r;
     }
 }
@@ -159,10 +175,11 @@ template <int DYN, bool OBS>
 __device__ __forceinline__ void batched_dispatch_seg(const DevProblem& P, const BatchInstance& I,
                                                      const BatchConsts& C, const float4* sched, int b, float* sM,
                                                      float* sFit, float2* sList, float4* sRed, float* sh, int* scan,
-                                                     int* s_count, d4orm_verdict* s_verdict, BatchResult* results)
+                                                     int* s_count, d4orm_verdict* s_verdict, BatchResult* results,
+                                                     long long t_launch, int* s_stop)
 {
 #define D4_CASE(SEGV) batched_instance<DYN, SEGV, OBS>(P, I, C, sched, b, sM, sFit, sList, sRed, sh, scan, s_count, \
-                                                  s_verdict, results)
+                                                  s_verdict, results, t_launch, s_stop)
     if (P.n <= 2) D4_CASE(2);
     else if (P.n <= 4) D4_CASE(4);
     else if (P.n <= 8) D4_CASE(8);
@@ -180,13 +197,17 @@ k_batched_solve(const DevProblem* __restrict__ probs, const BatchInstance* __res
     __shared__ DevProblem sP;
     __shared__ float sh[66];
     __shared__ int scan[33];
-    __shared__ int s_pick, s_count;
+    __shared__ int s_pick, s_count, s_stop;
     __shared__ d4orm_verdict s_verdict;
+    __shared__ long long s_launch;
     extern __shared__ float4 dyn_smem[];
     float* sM = reinterpret_cast<float*>(dyn_smem);                 // [C.ctrl_cap]
     float* sFit = sM + C.ctrl_cap;                                  // [C.n_cap]
     float2* sList = reinterpret_cast<float2*>(sFit + C.n_cap);      // [C.n_cap]
     float4* sRed = reinterpret_cast<float4*>(sList + C.n_cap);      // [32 warps][32]
+    if (threadIdx.x == 0) s_launch = globaltimer_ns();  // every CTA is resident from the launch on
+    __syncthreads();
+    const long long t_launch = s_launch;
     for (;;) {
         if (threadIdx.x == 0) s_pick = atomicAdd(queue, 1);
         __syncthreads();
@@ -201,19 +222,19 @@ k_batched_solve(const DevProblem* __restrict__ probs, const BatchInstance* __res
         switch (sP.dyn) {
         case HOLO2D:
             batched_dispatch_seg<HOLO2D, OBS>(sP, I, C, sched, b, sM, sFit, sList, sRed, sh, scan, &s_count, &s_verdict,
-                                         results);
+                                         results, t_launch, &s_stop);
             break;
         case HOLO3D:
             batched_dispatch_seg<HOLO3D, OBS>(sP, I, C, sched, b, sM, sFit, sList, sRed, sh, scan, &s_count, &s_verdict,
-                                         results);
+                                         results, t_launch, &s_stop);
             break;
         case UNICYCLE:
             batched_dispatch_seg<UNICYCLE, OBS>(sP, I, C, sched, b, sM, sFit, sList, sRed, sh, scan, &s_count,
-                                           &s_verdict, results);
+                                           &s_verdict, results, t_launch, &s_stop);
             break;
         default:
             batched_dispatch_seg<DIFFDRIVE4, OBS>(sP, I, C, sched, b, sM, sFit, sList, sRed, sh, scan, &s_count,
-                                             &s_verdict, results);
+                                             &s_verdict, results, t_launch, &s_stop);
             break;
         }
         __syncthreads();

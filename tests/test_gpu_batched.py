@@ -169,9 +169,59 @@ def test_batched_argument_errors(torch, g):
     out = torch.zeros((inst.T, inst.n, 2), device="cuda")
     with pytest.raises(g.D4ormError):
         g.d4orm_batch_solve(batch, g.Budget(max_iters=0), [out])
-    with pytest.raises(g.D4ormError) as ei:
-        g.d4orm_batch_solve(batch, g.Budget(max_iters=1, deadline_ms=5.0), [out])
-    assert ei.value.status == 2
     g.d4orm_batch_destroy(batch)
     res = g.d4orm_solve_batched([p.handle], g.Params(n_samples=64, n_steps=10), g.Budget(max_iters=1), [out])
     assert res[0]["iters_run"] == 1
+
+
+def test_batched_cancel_and_deadline(torch, g):
+    """Anytime stops of the persistent solve, injected from the host only:
+    a cancel request made before the launch stops every problem at its
+    first step (D4ORM_ERR_CANCELLED, no iteration, zero plans) and is
+    consumed; a deadline of 1 ns leaves every problem without an iteration
+    (D4ORM_ERR_TIMEOUT); a deadline far away changes nothing, bit for bit."""
+    insts = _mixed(5, seed=31, N=128, K=8)
+    probs = [g.Problem(i) for i in insts]
+    params = g.Params(n_samples=128, n_steps=8, seed=1, instance_tag=3)
+    outs = [torch.full((i.T, i.n, i.dims[1]), 7.0, device="cuda") for i in insts]
+    batch = g.d4orm_batch_create([p.handle for p in probs], params)
+    ref = g.d4orm_batch_solve(batch, g.Budget(max_iters=2), outs)
+    ref_plans = [o.clone() for o in outs]
+    assert all(r["stop_reason"] == g.STOP_BUDGET and r["iters_run"] == 2 for r in ref)
+
+    g.d4orm_batch_cancel(batch)
+    with pytest.raises(g.D4ormError) as ei:
+        g.d4orm_batch_solve(batch, g.Budget(max_iters=2), outs)
+    assert ei.value.status == g.ERR_CANCELLED
+    assert all(r["stop_reason"] == g.STOP_CANCELLED and r["iters_run"] == 0 for r in ei.value.results)
+    assert all(float(o.abs().max()) == 0.0 for o in outs)
+    again = g.d4orm_batch_solve(batch, g.Budget(max_iters=2), outs)    # the request was consumed
+    assert all(r["iters_run"] == 2 for r in again)
+    assert all(torch.equal(o, r) for o, r in zip(outs, ref_plans))
+
+    with pytest.raises(g.D4ormError) as ei:
+        g.d4orm_batch_solve(batch, g.Budget(max_iters=2, deadline_ms=1e-6), outs)
+    assert ei.value.status == g.ERR_TIMEOUT
+    assert all(r["stop_reason"] == g.STOP_DEADLINE and r["iters_run"] == 0 for r in ei.value.results)
+
+    far = g.d4orm_batch_solve(batch, g.Budget(max_iters=2, deadline_ms=1e9), outs)
+    assert all(r["stop_reason"] == g.STOP_BUDGET and r["iters_run"] == 2 for r in far)
+    assert all(torch.equal(o, r) for o, r in zip(outs, ref_plans))
+    g.d4orm_batch_destroy(batch)
+
+
+def test_single_solve_cancel(torch, g):
+    """d4orm_problem_cancel before a solve: D4ORM_ERR_CANCELLED with no
+    iteration and the zero plan; the request is consumed by that solve."""
+    inst = round_instance(scenarios.holo2d_circle_n4())
+    prob = g.Problem(inst)
+    p = gpu_params(g, inst)
+    u = torch.full((inst.T, inst.n, 2), 3.0, device="cuda")
+    g.d4orm_problem_cancel(prob.handle)
+    with pytest.raises(g.D4ormError) as ei:
+        g.d4orm_solve(prob.handle, p, g.Budget(max_iters=2, stop_on_success=True), u)
+    assert ei.value.status == g.ERR_CANCELLED
+    assert ei.value.results["iters_run"] == 0 and ei.value.results["stop_reason"] == g.STOP_CANCELLED
+    assert float(u.abs().max()) == 0.0
+    r = g.d4orm_solve(prob.handle, p, g.Budget(max_iters=2), u)
+    assert r["iters_run"] == 2 and r["stop_reason"] == g.STOP_BUDGET
