@@ -238,15 +238,19 @@ def reachable_box_instance(rng: np.random.Generator, n: int, T: int, N: int, *, 
 
 
 def warmstart_set(count: int, seed: int, N: int = 4096, T: int = 80, n_lo: int = 8, n_hi: int = 16,
-                  max_axis: float = 4.0, goal_tol: float = 0.5) -> list[Instance]:
+                  max_axis: float = 4.0, goal_tol: float = 0.5, large_share: float = 0.0,
+                  large_lo: int = 13) -> list[Instance]:
     """Teams of n ~ U{n_lo..n_hi} 2D holonomic robots for the learned warm
     start (training and held-out sets use disjoint seeds); goals within
     max_axis metres per axis of their starts; a plan reaches its goals when
-    every robot ends within goal_tol."""
+    every robot ends within goal_tol.  With large_share > 0 that share of the
+    teams draws n from U{large_lo..n_hi} instead (training sets that hold
+    enough of the largest teams)."""
     rng = np.random.default_rng(seed)
     out = []
     for _ in range(count):
-        inst = reachable_box_instance(rng, int(rng.integers(n_lo, n_hi + 1)), T, N, max_axis=max_axis)
+        lo = large_lo if large_share > 0.0 and rng.uniform() < large_share else n_lo
+        inst = reachable_box_instance(rng, int(rng.integers(lo, n_hi + 1)), T, N, max_axis=max_axis)
         inst.goal_tol = goal_tol
         out.append(inst)
     return out
