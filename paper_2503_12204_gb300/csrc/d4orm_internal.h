@@ -138,6 +138,8 @@ struct GemmArgs {
 };
 cudaError_t mlp_gemm(const void* A, bool a_bf16, const void* B, bool b_bf16, const GemmArgs& g, int splits,
                      cudaStream_t st);
+// True (and cleared) when a tensor-core GEMM gave up waiting for its MMAs.
+bool mlp_gemm_timed_out();
 cudaError_t mlp_sum_partials(const float* partial, int splits, long long MN, float* out, cudaStream_t st);
 cudaError_t mlp_colsum(const float* dY, int M, int N, float* db, cudaStream_t st);
 cudaError_t mlp_pool_concat(const void* H3, const float* mask, int B, int nmax, int W, void* C, cudaStream_t st);

@@ -193,6 +193,7 @@ d4orm_status read_loss(d4orm_warmstart* S, float* loss_host, cudaStream_t st)
     if (!loss_host) return D4ORM_OK;
     W_CUDA(cudaMemcpyAsync(S->h_loss, S->d_loss, sizeof(float), cudaMemcpyDeviceToHost, st));
     W_CUDA(cudaStreamSynchronize(st));
+    if (mlp_gemm_timed_out()) return set_error(D4ORM_ERR_TIMEOUT, "a tensor-core GEMM gave up waiting for its MMAs");
     *loss_host = *S->h_loss;
     return D4ORM_OK;
 }
@@ -415,6 +416,7 @@ d4orm_status d4orm_warmstart_predict(d4orm_warmstart* S, const d4orm_problem* pr
     const DevStep Si = make_step_consts(params, 0, start_step);
     W_CUDA(mlp_seed_from_output(S->Y, P.n, P.T, P.d_u, S->D, 1.0f / Si.c, du_seed_dev, st));
     W_CUDA(cudaStreamSynchronize(st));  // x, m are host stack buffers
+    if (mlp_gemm_timed_out()) return set_error(D4ORM_ERR_TIMEOUT, "a tensor-core GEMM gave up waiting for its MMAs");
     return D4ORM_OK;
 }
 

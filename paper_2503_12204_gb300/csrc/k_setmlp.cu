@@ -9,12 +9,13 @@
 //                      H5 = relu(H4 W5^T + b5), Y = H5 W6^T + b6 (T*d_u per robot)
 //   loss               masked mean squared error against the method's plan
 //
-// GEMMs run on the tensor cores with mma.sync m16n8k16 (BF16 operands, FP32
-// accumulation).  Operands are staged into shared memory as BF16 from
-// either BF16 or FP32 global tensors with arbitrary (row, column) strides,
-// so one kernel serves Y = A W^T (forward), dA = dY W (data gradient) and
-// dW = dY^T A (weight gradient, split over the reduction with per-split
-// partials summed in a fixed order).  Activations are stored in BF16, their
+// GEMMs run on the fifth-generation tensor cores (tcgen05.mma, BF16
+// operands, FP32 accumulation in tensor memory).  Operands are staged into
+// shared memory as BF16 from either BF16 or FP32 global tensors with
+// arbitrary (row, column) strides, so one kernel serves Y = A W^T
+// (forward), dA = dY W (data gradient) and dW = dY^T A (weight gradient,
+// split over the reduction with per-split partials summed in a fixed
+// order).  Activations are stored in BF16, their
 // gradients in FP32, the weights as FP32 masters with BF16 copies.
 #include <cuda_bf16.h>
 
@@ -25,9 +26,6 @@
 
 namespace d4orm {
 
-constexpr int kGBM = 64, kGBN = 64, kGBK = 32;  // CTA tile
-constexpr int kGPad = 8;                        // smem row padding (bf16)
-
 template <typename T> __device__ __forceinline__ float to_f(T v);
 template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
 template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
@@ -37,98 +35,195 @@ __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
-// D = A(16x16, row) * B(16x8, col) + D, BF16 x BF16 -> FP32
-__device__ __forceinline__ void mma_bf16_16816(float* d, const uint32_t* a, const uint32_t* b)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
 // C[m][n] = sum_k A(m, k) * B(n, k) over k in [k_begin, k_end), where
 // A(m, k) = A[m * a_rs + k * a_cs] and B(n, k) = B[n * b_rs + k * b_cs].
 // Epilogue (split == 1): + bias[n], relu, times (ref(m, n) > 0), then store
 // to out_f32 and/or out_bf16 (row stride ldc).  Split-K (gridDim.z > 1):
 // raw partial sums to partial[z][M][N].
 
+// ---------------------------------------------------------------------------
+// The GEMM runs on the fifth-generation tensor cores: tcgen05.mma (kind::f16,
+// BF16 x BF16 -> FP32, one CTA, M = 128) with the accumulator in tensor
+// memory.  The CTA (128 threads) stages each 128 x 64 (A) and 64 x 64 (B)
+// K-slice into shared memory as BF16 in the canonical no-swizzle K-major
+// layout -- 8-row x 16-byte core matrices, 128 B apart along K and 1 KB
+// apart along rows -- converting from FP32 where needed and honouring the
+// arbitrary strides (which is why the threads stage the operands rather
+// than TMA).  One thread issues the four K = 16 MMAs of the slice and
+// commits them to an mbarrier; the CTA waits on it (bounded) before the
+// slice's shared memory is refilled.  The epilogue reads the accumulator
+// back with tcgen05.ld (warp w owns rows 32w..32w+31) and applies the bias,
+// ReLU, ReLU-gradient mask or split-K partial store.
+// ---------------------------------------------------------------------------
+constexpr int kTBM = 128, kTBN = 64, kTBK = 64;
+// Dynamic shared memory requested per CTA: the staged operands (24 KB)
+// plus padding that keeps at most 4 CTAs on an SM, so 4 x 64 tensor-memory
+// columns never exceed the SM's 512 and tcgen05.alloc never waits.
+constexpr int kTcSmemLaunch = 52 * 1024;
+// set when an MMA completion wait gave up (read by mlp_gemm_timed_out)
+__device__ int g_tc_timeout;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// tcgen05 shared-memory matrix descriptor: start address, leading (K) and
+// stride (row-group) byte offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t tc_smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo & 0x3FFFF) >> 4) << 16) |
+           ((uint64_t)((sbo & 0x3FFFF) >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B,
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// byte offset of element (r, k) of a staged [rows][64] K-major slice
+__device__ __forceinline__ uint32_t tc_off(int r, int k)
+{
+    return (uint32_t)((r >> 3) * (kTBK / 8) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// Stage rows [0, ROWS) x k [k0, k0 + 64) of X(r, k) = X[(r0 + r) * rs + k * cs]
+// (zero outside [0, rmax) x [k0, ke)), 8 consecutive k per 16-byte store.
+template <int ROWS, typename T>
+__device__ __forceinline__ void tc_stage(uint8_t* s, const T* __restrict__ X, int r0, int rmax, long long rs,
+                                         long long cs, int k0, int ke)
+{
+    for (int i = threadIdx.x; i < ROWS * (kTBK / 8); i += blockDim.x) {
+        const int r = i % ROWS, j = i / ROWS;
+        const int gr = r0 + r;
+        uint32_t w[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int k = k0 + 8 * j + 2 * h;
+            const float lo = (gr < rmax && k < ke) ? to_f(X[gr * rs + k * cs]) : 0.0f;
+            const float hi = (gr < rmax && k + 1 < ke) ? to_f(X[gr * rs + (k + 1) * cs]) : 0.0f;
+            w[h] = pack_bf16(__float2bfloat16_rn(lo), __float2bfloat16_rn(hi));
+        }
+        *reinterpret_cast<uint4*>(s + tc_off(r, 8 * j)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity)
+{
+    // bounded: 2^22 polls, far beyond the microseconds an MMA slice takes
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
 
 template <typename TA, typename TB>
 __global__ void __launch_bounds__(128)
-k_gemm_bf16(const TA* __restrict__ A, const TB* __restrict__ B, const GemmArgs g)
+k_gemm_tc(const TA* __restrict__ A, const TB* __restrict__ B, const GemmArgs g)
 {
-    __shared__ __nv_bfloat16 sA[kGBM][kGBK + kGPad];
-    __shared__ __nv_bfloat16 sB[kGBN][kGBK + kGPad];
+    extern __shared__ __align__(1024) uint8_t tc_smem[];
+    uint8_t* sA = tc_smem;
+    uint8_t* sB = tc_smem + kTBM * kTBK * 2;
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.y * kGBM, n0 = blockIdx.x * kGBN;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;  // 2x2 warps, 32x32 each
+    const int m0 = blockIdx.y * kTBM, n0 = blockIdx.x * kTBN;
     const int splits = gridDim.z;
-    const int kchunk = ((g.K + splits - 1) / splits + kGBK - 1) / kGBK * kGBK;
+    const int kchunk = ((g.K + splits - 1) / splits + kTBK - 1) / kTBK * kTBK;
     const int kb = blockIdx.z * kchunk, ke = min(g.K, kb + kchunk);
-    float acc[2][4][4] = {};
-    const int grp = lane >> 2, tig = lane & 3;
-    for (int k0 = kb; k0 < ke; k0 += kGBK) {
-        for (int i = tid; i < kGBM * kGBK; i += 128) {
-            const int r = i / kGBK, c = i % kGBK;
-            const int m = m0 + r, k = k0 + c;
-            const float v = (m < g.M && k < ke) ? to_f(A[m * g.a_rs + k * g.a_cs]) : 0.0f;
-            sA[r][c] = __float2bfloat16_rn(v);
-        }
-        for (int i = tid; i < kGBN * kGBK; i += 128) {
-            const int r = i / kGBK, c = i % kGBK;
-            const int n = n0 + r, k = k0 + c;
-            const float v = (n < g.N && k < ke) ? to_f(B[n * g.b_rs + k * g.b_cs]) : 0.0f;
-            sB[r][c] = __float2bfloat16_rn(v);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < kGBK; kk += 16) {
-            uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi) {
-                const int r = wm + mi * 16 + grp;
-                const int c = kk + tig * 2;
-                af[mi][0] = pack_bf16(sA[r][c], sA[r][c + 1]);
-                af[mi][1] = pack_bf16(sA[r + 8][c], sA[r + 8][c + 1]);
-                af[mi][2] = pack_bf16(sA[r][c + 8], sA[r][c + 9]);
-                af[mi][3] = pack_bf16(sA[r + 8][c + 8], sA[r + 8][c + 9]);
-            }
-#pragma unroll
-            for (int ni = 0; ni < 4; ++ni) {
-                const int n = wn + ni * 8 + grp;
-                const int c = kk + tig * 2;
-                bfr[ni][0] = pack_bf16(sB[n][c], sB[n][c + 1]);
-                bfr[ni][1] = pack_bf16(sB[n][c + 8], sB[n][c + 9]);
-            }
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-                for (int ni = 0; ni < 4; ++ni) mma_bf16_16816(acc[mi][ni], af[mi], bfr[ni]);
-        }
-        __syncthreads();
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                     "r"(kTBN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base, mb = smem_addr(&mbar);
+    constexpr uint32_t idesc = tc_idesc(kTBM, kTBN);
+    uint32_t parity = 0;
+    bool ok = true, any = false;
+    for (int k0 = kb; k0 < ke && ok; k0 += kTBK) {
+        tc_stage<kTBM>(sA, A, m0, g.M, g.a_rs, g.a_cs, k0, ke);
+        tc_stage<kTBN>(sB, B, n0, g.N, g.b_rs, g.b_cs, k0, ke);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic-proxy writes -> tensor core
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
+            for (int s = 0; s < kTBK / 16; ++s) {
+                const uint64_t da = tc_smem_desc(smem_addr(sA) + s * 256, 128, (kTBK / 8) * 128);
+                const uint64_t db = tc_smem_desc(smem_addr(sB) + s * 256, 128, (kTBK / 8) * 128);
+                const uint32_t accumulate = (any || s > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
+                         : "memory");
+        }
+        any = true;
+        const bool mine = tc_wait(mb, parity);
+        parity ^= 1u;
+        ok = __syncthreads_and(mine) != 0;  // one verdict for the whole CTA
+        if (!ok && tid == 0) atomicExch(&g_tc_timeout, 1);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const int m = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c = 0; c < kTBN; c += 8) {
+            float v[8];
+            if (any) {
+                uint32_t r[8];
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                               "=r"(r[7])
+                             : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int ni = 0; ni < 4; ++ni)
+                for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+            } else {
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int m = m0 + wm + mi * 16 + grp + (h >= 2 ? 8 : 0);
-                const int n = n0 + wn + ni * 8 + tig * 2 + (h & 1);
-                if (m >= g.M || n >= g.N) continue;
-                float v = acc[mi][ni][h];
+                for (int i = 0; i < 8; ++i) v[i] = 0.0f;  // an empty K range
+            }
+            if (m >= g.M) continue;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int n = n0 + c + i;
+                if (n >= g.N) continue;
+                float x = v[i];
                 if (splits > 1) {
-                    g.partial[((long long)blockIdx.z * g.M + m) * g.N + n] = v;
+                    g.partial[((long long)blockIdx.z * g.M + m) * g.N + n] = x;
                     continue;
                 }
-                if (g.bias) v += g.bias[n];
-                if (g.relu) v = fmaxf(v, 0.0f);
+                if (g.bias) x += g.bias[n];
+                if (g.relu) x = fmaxf(x, 0.0f);
                 if (g.ref && !(__bfloat162float(static_cast<const __nv_bfloat16*>(g.ref)[m * g.ldc + n]) > 0.0f))
-                    v = 0.0f;
-                if (g.out_f32) g.out_f32[m * g.ldc + n] = v;
-                if (g.out_bf16) static_cast<__nv_bfloat16*>(g.out_bf16)[m * g.ldc + n] = __float2bfloat16_rn(v);
+                    x = 0.0f;
+                if (g.out_f32) g.out_f32[m * g.ldc + n] = x;
+                if (g.out_bf16) static_cast<__nv_bfloat16*>(g.out_bf16)[m * g.ldc + n] = __float2bfloat16_rn(x);
             }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTBN) : "memory");
 }
 
 // out[m][n] = sum_z partial[z][m][n]   (fixed order)
@@ -260,11 +355,28 @@ __global__ void k_seed_from_output(const float* __restrict__ Y, int n, int T, in
 
 // ------------------------------------------------------------------ launchers
 
+bool mlp_gemm_timed_out()
+{
+    int flag = 0;
+    if (cudaMemcpyFromSymbol(&flag, g_tc_timeout, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (flag) {
+        const int zero = 0;
+        cudaMemcpyToSymbol(g_tc_timeout, &zero, sizeof(int));
+    }
+    return flag != 0;
+}
+
 template <typename TA, typename TB>
 static cudaError_t gemm_launch(const TA* A, const TB* B, GemmArgs g, int splits, cudaStream_t st)
 {
-    dim3 grid((g.N + kGBN - 1) / kGBN, (g.M + kGBM - 1) / kGBM, splits);
-    k_gemm_bf16<TA, TB><<<grid, 128, 0, st>>>(A, B, g);
+    static cudaError_t attr =
+        cudaFuncSetAttribute(k_gemm_tc<TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemLaunch);
+    if (attr != cudaSuccess) return attr;
+    dim3 grid((g.N + kTBN - 1) / kTBN, (g.M + kTBM - 1) / kTBM, splits);
+    k_gemm_tc<TA, TB><<<grid, 128, kTcSmemLaunch, st>>>(A, B, g);
     return cudaGetLastError();
 }
 
