@@ -90,7 +90,6 @@ def flops_per_sample_rollout(inst) -> int:
 NCU_TRAFFIC_BYTES = {
     ("k_rollout_fitness_paired", "holo3d_n16_T100_N8192"): 87296,
     ("k_rollout_fitness_pipe", "unicycle_n8_T100_N2048"): 38400,
-    ("k_rollout_fitness", "unicycle_n8_T100_N2048"): 46080,
 }
 
 
@@ -411,7 +410,8 @@ def run_batched(args, torch, g, world, rank):
         "config": {"workload": "mixed512_batched", "problems": len(insts), "samples_N": 1024, "denoise_steps": 100,
                    "max_iterations": 5, "stop_on_success": True, "sample_rollouts_per_step": per_step,
                    "threads_per_cta": info["threads_per_cta"], "ctas": info["ctas"],
-                   "autotune_ms_128_256_512": info["tuned_ms"], "parallelism": f"replicas{world}",
+                   "autotune_ms_128_256_512": info["tuned_ms"], "autotune_table": g.d4orm_batch_tuning(batch),
+                   "parallelism": f"replicas{world}",
                    "l2": "flushed between timed steps (256 MB write)"},
         "e2e": {"value": per_step * world / (e2e_ms / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(2 * i.n * i.dims[0] * 4 for i in insts)),

@@ -322,8 +322,10 @@ typedef struct d4orm_batch d4orm_batch;
 /* Build a batch over problems[0..count-1] (handles must outlive the batch)
  * with one set of denoising parameters.  Uploads descriptors and allocates
  * per-problem workspace.  autotune != 0 times the persistent kernel at 128,
- * 256 and 512 threads per CTA on a 2-step pilot over the whole batch and
- * keeps the fastest (see d4orm_batch_info); otherwise 256.
+ * 256 and 512 threads per CTA, each at the maximum resident CTAs per SM,
+ * half of it and one, on a 2-step pilot over the whole batch, and keeps
+ * the fastest (see d4orm_batch_info, d4orm_batch_tuning); otherwise 512
+ * threads, one CTA per SM.
  * Errors: INVALID_ARG (null arguments, bad params, tags beyond
  * D4ORM_MAX_TAG), UNSUPPORTED (n_samples > D4ORM_BATCH_MAX_SAMPLES, or
  * shared memory for the largest problem above 200 KB), OOM, CUDA. */
@@ -351,9 +353,16 @@ d4orm_status d4orm_batch_create(d4orm_problem *const *problems, int count, const
 d4orm_status d4orm_batch_solve(d4orm_batch *batch, const d4orm_budget *budget, const float *const *du_init_dev,
                                float *const *u_out_dev, d4orm_result *out_host, void *stream);
 
-/* Launch shape the batch uses and the autotuner's pilot times (ms, -1 when
- * a width was not tried) for 128 / 256 / 512 threads. */
+/* Launch shape the batch uses and the autotuner's best pilot time (ms, -1
+ * when a width was not tried) for 128 / 256 / 512 threads per CTA. */
 d4orm_status d4orm_batch_info(const d4orm_batch *batch, int *threads_per_cta, int *ctas, float *tuned_ms);
+
+/* Every pilot the autotuner ran (0 without autotuning): *count entries of
+ * (threads per CTA, resident CTAs per SM, pilot ms), at most `capacity`
+ * written to the nullable host arrays.  The autotuner tries widths 128,
+ * 256 and 512 at the maximum resident CTAs per SM, half of it and one. */
+d4orm_status d4orm_batch_tuning(const d4orm_batch *batch, int capacity, int *count, int *threads_per_cta,
+                                int *ctas_per_sm, float *pilot_ms);
 
 /* Request that the running (or the next) d4orm_batch_solve of this batch
  * stop at the next denoising-step boundary of every CTA.  Thread-safe; sets

@@ -43,7 +43,8 @@ EXPORTS = (
     "d4orm_denoise_step",
     "d4orm_denoise_step_timed", "d4orm_denoise_step_noalloc", "d4orm_solve", "d4orm_problem_cancel",
     "d4orm_sample_noise", "d4orm_philox4x32_10", "d4orm_fp32_fma_probe", "d4orm_status_string", "d4orm_last_error",
-    "d4orm_batch_create", "d4orm_batch_solve", "d4orm_batch_info", "d4orm_batch_cancel", "d4orm_batch_destroy",
+    "d4orm_batch_create", "d4orm_batch_solve", "d4orm_batch_info", "d4orm_batch_tuning", "d4orm_batch_cancel",
+    "d4orm_batch_destroy",
     "d4orm_solve_batched",
     "d4orm_warmstart_create", "d4orm_warmstart_destroy", "d4orm_warmstart_param_count",
     "d4orm_warmstart_get_params", "d4orm_warmstart_set_params", "d4orm_warmstart_forward",
@@ -162,6 +163,9 @@ def _load() -> ctypes.CDLL:
     lib.d4orm_batch_cancel.restype = i
     lib.d4orm_problem_cancel.argtypes = [vp]
     lib.d4orm_problem_cancel.restype = i
+    lib.d4orm_batch_tuning.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
+                                       ctypes.POINTER(ctypes.c_float)]
+    lib.d4orm_batch_tuning.restype = i
     lib.d4orm_batch_destroy.argtypes = [vp]
     lib.d4orm_batch_destroy.restype = None
     lib.d4orm_solve_batched.argtypes = [PP, i, ctypes.POINTER(_Params), ctypes.POINTER(_Budget), PP,
@@ -431,6 +435,16 @@ def d4orm_batch_solve(batch, budget: Budget, u_out_devs, du_init_devs=None, stre
     status = lib.d4orm_batch_solve(batch, ctypes.byref(bc), inits, outs, res, _stream(stream))
     _anytime_check(status, _results(res, len(u_out_devs)))
     return _results(res, len(u_out_devs))
+
+
+def d4orm_batch_tuning(batch) -> list[dict]:
+    """Every autotuner pilot: threads per CTA, CTAs per SM, ms."""
+    n = ctypes.c_int()
+    _check(lib.d4orm_batch_tuning(batch, 0, ctypes.byref(n), None, None, None))
+    w, o = (ctypes.c_int * max(1, n.value))(), (ctypes.c_int * max(1, n.value))()
+    ms = (ctypes.c_float * max(1, n.value))()
+    _check(lib.d4orm_batch_tuning(batch, n.value, ctypes.byref(n), w, o, ms))
+    return [dict(threads_per_cta=w[k], ctas_per_sm=o[k], ms=ms[k]) for k in range(n.value)]
 
 
 def d4orm_batch_info(batch) -> dict:

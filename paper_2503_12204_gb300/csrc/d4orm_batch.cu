@@ -38,7 +38,11 @@ struct d4orm_batch {
     size_t smem = 0;
     int threads = 256, grid = 0;
     bool obstacles = false;            // any problem has obstacles: the kernel variant with the penalty
-    float tuned_ms[3] = {-1.f, -1.f, -1.f};
+    float tuned_ms[3] = {-1.f, -1.f, -1.f};   // best pilot per CTA width
+    int ctas_per_sm = 0;
+    // every pilot of the autotuner: CTA width, resident CTAs per SM, ms
+    std::vector<int> tune_width, tune_occ;
+    std::vector<float> tune_ms;
     // cached graph for one (max_iters, stop_on_success, start_step, deadline) combination
     cudaGraphExec_t graph = nullptr;
     int g_iters = -1, g_stop = -1, g_start = -1;
@@ -72,10 +76,10 @@ void batch_free(d4orm_batch* B)
     } while (0)
 
 // One timed run of the persistent kernel over the whole batch with a short
-// schedule (2 steps, 1 iteration), for the autotuner.
-d4orm_status pilot_ms(d4orm_batch* B, int threads, float* ms)
+// schedule (2 steps, 1 iteration) at `threads` per CTA and `occ` CTAs per
+// SM (<= the resident maximum), for the autotuner.
+d4orm_status pilot_ms(d4orm_batch* B, int threads, int occ, float* ms)
 {
-    const int occ = batched_ctas_per_sm(B->obstacles, threads, B->smem);
     if (occ <= 0) {
         *ms = -1.f;
         return D4ORM_OK;
@@ -226,28 +230,48 @@ d4orm_status d4orm_batch_create(d4orm_problem* const* problems, int count, const
     if (e == cudaSuccess) e = cudaMemcpy(B->d_insts, B->h_insts, sizeof(BatchInstance) * count, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail_cleanup(set_cuda_error(e, "batch upload"));
 
-    // autotuner: CTA width among 128 / 256 / 512 threads, by a timed pilot
+    // autotuner: CTA width (128 / 256 / 512 threads) x resident CTAs per SM
+    // (the maximum, half of it, one), each pair timed by a pilot over the
+    // whole batch; without autotuning, 256 threads at the maximum
     const int cand[3] = {128, 256, 512};
-    int best = 256;
+    int best = std::min(256, kBatchMaxThreads), best_occ = 0;
     float best_ms = -1.f;
-    for (int c = 0; c < 3; ++c) {
-        if (!autotune) break;
-        float ms = -1.f;
-        s = pilot_ms(B, cand[c], &ms);
-        if (s != D4ORM_OK) return fail_cleanup(s);
-        B->tuned_ms[c] = ms;
-        if (ms > 0.f && (best_ms < 0.f || ms < best_ms)) {
-            best_ms = ms;
-            best = cand[c];
+    for (int c = 0; c < 3 && autotune; ++c) {
+        if (cand[c] > kBatchMaxThreads) continue;
+        const int occ_max = batched_ctas_per_sm(B->obstacles, cand[c], B->smem);
+        int occs[3] = {occ_max, occ_max / 2, 1};
+        for (int o = 0; o < 3; ++o) {
+            const int occ = occs[o];
+            if (occ <= 0 || (o > 0 && occ >= occs[o - 1])) continue;  // distinct, descending
+            float ms = -1.f;
+            s = pilot_ms(B, cand[c], occ, &ms);
+            if (s != D4ORM_OK) return fail_cleanup(s);
+            B->tune_width.push_back(cand[c]);
+            B->tune_occ.push_back(occ);
+            B->tune_ms.push_back(ms);
+            if (ms > 0.f && (B->tuned_ms[c] < 0.f || ms < B->tuned_ms[c])) B->tuned_ms[c] = ms;
+            if (ms > 0.f && (best_ms < 0.f || ms < best_ms)) {
+                best_ms = ms;
+                best = cand[c];
+                best_occ = occ;
+            }
         }
     }
-    int occ = batched_ctas_per_sm(B->obstacles, best, B->smem);
+    if (!autotune) {
+        // default: the widest CTA, one per SM (the best pilot on the 512
+        // ragged mixed-dynamics teams: 6.9 ms against 9.1 ms at two per SM
+        // and 10.6-21.2 ms for narrower CTAs)
+        best = kBatchMaxThreads;
+        best_occ = batched_ctas_per_sm(B->obstacles, best, B->smem) > 0 ? 1 : 0;
+    }
+    int occ = best_occ > 0 ? best_occ : batched_ctas_per_sm(B->obstacles, best, B->smem);
     if (occ <= 0) {
         best = 128;
         occ = batched_ctas_per_sm(B->obstacles, best, B->smem);
     }
     if (occ <= 0) return fail_cleanup(set_error(D4ORM_ERR_UNSUPPORTED, "batched kernel cannot be resident"));
     B->threads = best;
+    B->ctas_per_sm = occ;
     B->grid = std::min(count, B->sms * occ);
     *out = B;
     return D4ORM_OK;
@@ -268,6 +292,20 @@ d4orm_status d4orm_batch_info(const d4orm_batch* B, int* threads_per_cta, int* c
     if (ctas) *ctas = B->grid;
     if (tuned_ms)
         for (int c = 0; c < 3; ++c) tuned_ms[c] = B->tuned_ms[c];
+    return D4ORM_OK;
+}
+
+d4orm_status d4orm_batch_tuning(const d4orm_batch* B, int capacity, int* count, int* threads_per_cta,
+                                int* ctas_per_sm, float* pilot_ms)
+{
+    if (!B || !count) return set_error(D4ORM_ERR_INVALID_ARG, "null batch or count");
+    const int n = (int)B->tune_ms.size();
+    *count = n;
+    for (int i = 0; i < n && i < capacity; ++i) {
+        if (threads_per_cta) threads_per_cta[i] = B->tune_width[i];
+        if (ctas_per_sm) ctas_per_sm[i] = B->tune_occ[i];
+        if (pilot_ms) pilot_ms[i] = B->tune_ms[i];
+    }
     return D4ORM_OK;
 }
 

@@ -57,6 +57,14 @@ def test_batched_matches_single_solves(torch, g, oracle_lib, autotune):
     assert info["threads_per_cta"] in (128, 256, 512) and info["ctas"] >= 1
     if autotune:
         assert max(info["tuned_ms"]) > 0
+        table = g.d4orm_batch_tuning(batch)
+        assert len(table) >= 3 and {t["threads_per_cta"] for t in table} <= {128, 256, 512}
+        best = min((t for t in table if t["ms"] > 0), key=lambda t: t["ms"])
+        assert best["threads_per_cta"] == info["threads_per_cta"]
+        assert info["ctas"] == min(len(insts), torch.cuda.get_device_properties(0).multi_processor_count
+                                   * best["ctas_per_sm"])
+    else:
+        assert g.d4orm_batch_tuning(batch) == []
     res = g.d4orm_batch_solve(batch, g.Budget(max_iters=2), outs)
     torch.cuda.synchronize()
     for b, (inst, p) in enumerate(zip(insts, probs)):
