@@ -68,7 +68,9 @@ def sweep(torch, dynamics=DYNAMICS, robots=(10, 16), steps=(50, 100, 200), runs:
                 rate = [sum(1 for f in first if 0 <= f < i) / runs for i in range(1, max_iters + 1)]
                 rows.append(dict(dynamics=dyn, robots=n, steps=K, success_within_iters=rate,
                                  collision_free_final=sum(r["verdict"]["collision_free"] for r in res) / runs,
-                                 wall_s=wall))
+                                 wall_s=wall, runs=[dict(first_success_iter=r["first_success_iter"],
+                                                         iters_run=r["iters_run"], verdict=r["verdict"])
+                                                    for r in res]))
                 log(f"{dyn} n={n} K={K}: success within 1..{max_iters} iterations {rate}")
             for p in probs:
                 p.close()

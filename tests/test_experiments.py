@@ -69,3 +69,33 @@ def test_held_out_team_selection():
     assert [t.n for t in big] == [t.n for t in all_teams if t.n >= 15][:4]
     assert all(t.n >= 15 for t in big)
 
+
+
+@pytest.mark.gpu
+def test_sweep_cell_matches_oracle_solves(oracle_lib):
+    """One cell of the sensitivity sweep (its own instance builder, batch
+    and tallies) against orc_solve of each run (run b = instance tag b,
+    seed 0, the sweep's w and lambda): two iterations of K = 4 steps keep
+    FP32 and FP64 plans close, so every run's final Eq. (3) reward agrees
+    within 2e-3 and its collision-free flag and first success match."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("CUDA device required")
+    from helpers import build_library, oracle_params, oracle_problem
+    build_library()
+    from paper_2503_12204_gb300 import sweep as SW
+    K, runs, iters, N = 4, 3, 2, 256
+    rows = SW.sweep(torch, dynamics=("holo2d", "holo3d"), robots=(6,), steps=(K,), runs=runs, max_iters=iters,
+                    N=N, log=lambda m: None)
+    for row in rows:
+        inst = SW.instance(row["dynamics"], 6, N)
+        inst.K, inst.w_safe, inst.lam, inst.seed = K, 1.0, 0.3, 0
+        for b, run in enumerate(row["runs"]):
+            inst.tag = b
+            _, vs, first = oracle_lib.solve(oracle_problem(oracle_lib, inst), oracle_params(oracle_lib, inst), iters,
+                                            stop_on_success=True)
+            vg, vo = run["verdict"], vs[-1]
+            assert run["first_success_iter"] == first and run["iters_run"] == len(vs)
+            assert abs(vg["reward"] - vo["reward"]) <= 2e-3 * abs(vo["reward"]) + 1e-5, (row["dynamics"], b)
+            if abs(vo["min_pair_dist"] - 2 * inst.radius) > 2e-4:
+                assert vg["collision_free"] == vo["collision_free"]
