@@ -90,6 +90,7 @@ def flops_per_sample_rollout(inst) -> int:
 NCU_TRAFFIC_BYTES = {
     ("k_rollout_fitness_paired", "holo3d_n16_T100_N8192"): 87296,
     ("k_rollout_fitness_pipe", "unicycle_n8_T100_N2048"): 38400,
+    ("k_rollout_fitness", "unicycle_n8_T100_N2048"): 45824,
 }
 
 
@@ -114,7 +115,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu_index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except (OSError, FileNotFoundError):
