@@ -45,7 +45,7 @@ extern "C" {
 typedef enum {
     D4ORM_OK = 0,
     D4ORM_ERR_INVALID_ARG = 1,  /* null pointer, size out of range, bad enum  */
-    D4ORM_ERR_UNSUPPORTED = 2,  /* valid but beyond this build's limits       */
+    D4ORM_ERR_UNSUPPORTED = 2,  /* valid but beyond the library's limits     */
     D4ORM_ERR_OOM = 3,          /* device or pinned allocation failed         */
     D4ORM_ERR_CUDA = 4,         /* a CUDA call failed (see d4orm_last_error)  */
     D4ORM_ERR_TIMEOUT = 5,      /* a bounded device wait expired              */

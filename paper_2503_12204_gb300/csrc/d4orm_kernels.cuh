@@ -69,13 +69,14 @@ __device__ __forceinline__ void block_reduce_sum_max(float& s, float& m, float* 
     __syncthreads();
 }
 
-// Samples whose unnormalised weight exp(l_j - max l) falls below 2^-36
+// Samples whose unnormalised weight exp(l_j - max l) falls below 2^-30
 // are left out of the weighted sum: together they move it by at most
-// N * 2^-36 * max|eps| / Z (under 1e-6 of the largest weight for N <= 65536),
-// below the rounding of the binary32 sum, and typically most samples of a
-// batch are that far below the best one, so the noise they would need is
-// never regenerated.
-constexpr float kLogWeightCut = -24.953298f;  // -36 ln 2
+// N * 2^-30 * max|eps| relative to the largest weight (max|eps| <= 5.77 for
+// the 24-bit Box-Muller inputs: under 4.5e-5 for N <= 8192 and 3.5e-4 for
+// N <= 65536, against the 1e-3 tolerance of the update), and typically a
+// large share of a batch is that far below the best sample, so the noise
+// those samples would need is never regenerated.
+constexpr float kLogWeightCut = -20.794415f;  // -30 ln 2
 
 // ---------------------------------------------------------------------------
 // Batch normalisation (Sec. IV-C) + temperature softmax (Eq. (6)) of the N
@@ -227,8 +228,8 @@ __device__ __forceinline__ float sample_fitness_segment(const DevProblem& P, con
         integrate<DYN>(x, u, P);
         // Eq. (4): goal term, accumulated before the pair tests so that it
         // does not wait for their shuffle chain (on the latency-bound
-        // unicycle workload this ordering took the kernel from 18.5 to
-        // 16.5 us)
+        // unicycle workload this ordering took the kernel from 15.9 to
+        // 15.0 us inside the solve's CUDA graph)
         float dg2 = 0.0f;
 #pragma unroll
         for (int d = 0; d < DP; ++d) {

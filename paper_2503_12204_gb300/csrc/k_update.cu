@@ -5,7 +5,7 @@
 // softmax of Eq. (6), as a two-pass log-sum-exp (maximum logit first).
 //
 // Pass 1 also compacts the samples that carry weight into an ordered
-// (weight, index) list; weights below 2^-36 of the largest are dropped.
+// (weight, index) list; weights below 2^-30 of the largest are dropped.
 //
 // Pass 2 (k_weighted_sum): S = sum_j w_j eps_j over the listed samples, with
 // eps regenerated from the same Philox counters K2 used (no sample is
