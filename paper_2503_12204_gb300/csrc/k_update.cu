@@ -58,8 +58,13 @@ k_weighted_sum(const DevProblem P, const DevStep S, const float2* __restrict__ l
     const int n_list = *count;
     const int stride = gridDim.y * kWSRows;
     float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-    for (int e = blockIdx.y * kWSRows + row; e < n_list; e += stride) {
-        const float2 wj = list[e];  // warp-uniform
+    // the next entry is loaded while the current sample's noise is
+    // regenerated (the Philox counter needs the sample index first)
+    int e = blockIdx.y * kWSRows + row;
+    float2 next = e < n_list ? list[e] : make_float2(0.0f, 0.0f);
+    for (; e < n_list; e += stride) {
+        const float2 wj = next;  // warp-uniform
+        if (e + stride < n_list) next = list[e + stride];
         float z[4];
         noise_quad(S, c3, (uint32_t)q, (uint32_t)__float_as_int(wj.y), (uint32_t)k, z);
         a0 = fmaf(wj.x, z[0], a0);
