@@ -335,6 +335,16 @@ def rollout_kernel_in_graph_ms(torch, g, prob, params, inst, du) -> float:
     return float(np.median(times))
 
 
+def packing_summary(g, batch, count):
+    """Problems rolled out two robots per lane and the autotuner's packing
+    pilots (summed device ms per bucket, one robot vs two per lane)."""
+    pk = g.d4orm_batch_packing(batch, count)
+    names = {g.HOLO2D: "holo2d", g.HOLO3D: "holo3d"}
+    return {"paired_problems": sum(pk["paired"]),
+            "pilot_ms_single_paired": {f"{names[d]}_{r}": [round(s * 1e-6, 3), round(q * 1e-6, 3)]
+                                       for (d, r), (s, q) in pk["bucket_ns"].items()}}
+
+
 def run_batched(args, torch, g, world, rank):
     """512 ragged problems (n ~ U{2..16}, T ~ U{40..120}, 40/30/30 % 2D
     holonomic / 3D holonomic / unicycle, 10 m box), N = 1024, 100 steps x up
@@ -412,6 +422,7 @@ def run_batched(args, torch, g, world, rank):
                    "max_iterations": 5, "stop_on_success": True, "sample_rollouts_per_step": per_step,
                    "threads_per_cta": info["threads_per_cta"], "ctas": info["ctas"],
                    "autotune_ms_128_256_512": info["tuned_ms"], "autotune_table": g.d4orm_batch_tuning(batch),
+                   "packing": packing_summary(g, batch, len(insts)),
                    "parallelism": f"replicas{world}",
                    "l2": "flushed between timed steps (256 MB write)"},
         "e2e": {"value": per_step * world / (e2e_ms / 1e3), "unit": UNIT,

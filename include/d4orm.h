@@ -324,8 +324,10 @@ typedef struct d4orm_batch d4orm_batch;
  * per-problem workspace.  autotune != 0 times the persistent kernel at 128,
  * 256 and 512 threads per CTA, each at the maximum resident CTAs per SM,
  * half of it and one, on a 2-step pilot over the whole batch, and keeps
- * the fastest (see d4orm_batch_info, d4orm_batch_tuning); otherwise 512
- * threads, one CTA per SM.
+ * the fastest (see d4orm_batch_info, d4orm_batch_tuning), then at that
+ * shape chooses the robot-lane packing per bucket of problems (see
+ * d4orm_batch_packing); otherwise 512 threads, one CTA per SM, two robots
+ * per lane wherever the kernel has that rollout.
  * Errors: INVALID_ARG (null arguments, bad params, tags beyond
  * D4ORM_MAX_TAG), UNSUPPORTED (n_samples > D4ORM_BATCH_MAX_SAMPLES, or
  * shared memory for the largest problem above 200 KB), OOM, CUDA. */
@@ -363,6 +365,28 @@ d4orm_status d4orm_batch_info(const d4orm_batch *batch, int *threads_per_cta, in
  * 256 and 512 at the maximum resident CTAs per SM, half of it and one. */
 d4orm_status d4orm_batch_tuning(const d4orm_batch *batch, int capacity, int *count, int *threads_per_cta,
                                 int *ctas_per_sm, float *pilot_ms);
+
+/* Robot-lane packing of the batched solver's sample rollouts.  SINGLE: one
+ * robot per lane.  PAIRED: two robots per lane, their dynamics and pair
+ * tests issued as packed f32x2 arithmetic; the kernel has this rollout for
+ * 2D/3D holonomic teams of 5..16 robots, and other problems keep one robot
+ * per lane.  Both give the same rewards up to the order of float sums. */
+enum { D4ORM_PACK_SINGLE = 0, D4ORM_PACK_PAIRED = 1 };
+
+/* Set the packing of every problem of the batch (overrides the
+ * autotuner's per-bucket choice; takes effect at the next solve).
+ * Synchronises the device.  Errors: INVALID_ARG (null batch, unknown
+ * mode), CUDA. */
+d4orm_status d4orm_batch_set_packing(d4orm_batch *batch, int mode);
+
+/* The packing each problem uses: paired[b] = 1 for two robots per lane (at
+ * most `capacity` entries, nullable).  bucket_ns (nullable, 8 entries): the
+ * autotuner's packing pilots, summed device ns of the problems of each
+ * bucket (2D holonomic 5..8 robots, 2D 9..16, 3D 5..8, 3D 9..16) with one
+ * and then two robots per lane; zeros without autotuning.  With
+ * autotuning a bucket is packed when its paired sum is the smaller;
+ * without it, every packable problem is. */
+d4orm_status d4orm_batch_packing(const d4orm_batch *batch, int capacity, int *paired, long long *bucket_ns);
 
 /* Request that the running (or the next) d4orm_batch_solve of this batch
  * stop at the next denoising-step boundary of every CTA.  Thread-safe; sets

@@ -23,6 +23,7 @@ HOLO2D, HOLO3D, UNICYCLE, DIFFDRIVE4 = 0, 1, 2, 3
 EULER, RK4 = 0, 1
 ROLLOUT_AUTO, ROLLOUT_REGISTER, ROLLOUT_PIPELINE, ROLLOUT_PAIRED = 0, 1, 2, 3
 STOP_BUDGET, STOP_DEADLINE, STOP_CANCELLED = 0, 1, 2
+PACK_SINGLE, PACK_PAIRED = 0, 1
 ERR_TIMEOUT, ERR_CANCELLED = 5, 6
 UPDATE_DENOISE, UPDATE_MPPI = 0, 1
 DIMS = {HOLO2D: (4, 2, 2), HOLO3D: (6, 3, 3), UNICYCLE: (3, 2, 2), DIFFDRIVE4: (4, 2, 2)}
@@ -44,7 +45,7 @@ EXPORTS = (
     "d4orm_denoise_step_timed", "d4orm_denoise_step_noalloc", "d4orm_solve", "d4orm_problem_cancel",
     "d4orm_sample_noise", "d4orm_philox4x32_10", "d4orm_fp32_fma_probe", "d4orm_status_string", "d4orm_last_error",
     "d4orm_batch_create", "d4orm_batch_solve", "d4orm_batch_info", "d4orm_batch_tuning", "d4orm_batch_cancel",
-    "d4orm_batch_destroy",
+    "d4orm_batch_set_packing", "d4orm_batch_packing", "d4orm_batch_destroy",
     "d4orm_solve_batched",
     "d4orm_warmstart_create", "d4orm_warmstart_destroy", "d4orm_warmstart_param_count",
     "d4orm_warmstart_get_params", "d4orm_warmstart_set_params", "d4orm_warmstart_forward",
@@ -166,6 +167,10 @@ def _load() -> ctypes.CDLL:
     lib.d4orm_batch_tuning.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                                        ctypes.POINTER(ctypes.c_float)]
     lib.d4orm_batch_tuning.restype = i
+    lib.d4orm_batch_set_packing.argtypes = [vp, i]
+    lib.d4orm_batch_set_packing.restype = i
+    lib.d4orm_batch_packing.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong)]
+    lib.d4orm_batch_packing.restype = i
     lib.d4orm_batch_destroy.argtypes = [vp]
     lib.d4orm_batch_destroy.restype = None
     lib.d4orm_solve_batched.argtypes = [PP, i, ctypes.POINTER(_Params), ctypes.POINTER(_Budget), PP,
@@ -445,6 +450,23 @@ def d4orm_batch_tuning(batch) -> list[dict]:
     ms = (ctypes.c_float * max(1, n.value))()
     _check(lib.d4orm_batch_tuning(batch, n.value, ctypes.byref(n), w, o, ms))
     return [dict(threads_per_cta=w[k], ctas_per_sm=o[k], ms=ms[k]) for k in range(n.value)]
+
+
+def d4orm_batch_set_packing(batch, mode: int) -> None:
+    """PACK_SINGLE or PACK_PAIRED for every problem (paired only where the
+    kernel has the two-robots-per-lane rollout)."""
+    _check(lib.d4orm_batch_set_packing(batch, int(mode)))
+
+
+def d4orm_batch_packing(batch, count: int) -> dict:
+    """Per-problem packing (1 = two robots per lane) and the packing
+    pilots' summed device ns per bucket: {(dyn, "5-8"|"9-16"): (single, paired)}."""
+    paired = (ctypes.c_int * max(1, count))()
+    ns = (ctypes.c_longlong * 8)()
+    _check(lib.d4orm_batch_packing(batch, count, paired, ns))
+    names = [(HOLO2D, "5-8"), (HOLO2D, "9-16"), (HOLO3D, "5-8"), (HOLO3D, "9-16")]
+    return dict(paired=[paired[b] for b in range(count)],
+                bucket_ns={names[k]: (ns[2 * k], ns[2 * k + 1]) for k in range(4)})
 
 
 def d4orm_batch_info(batch) -> dict:

@@ -17,6 +17,16 @@ namespace {
 
 int seg_of(int n) { return n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : 32; }
 
+// The batched kernel has a two-robots-per-lane rollout for holonomic teams
+// of 5..16 robots (8- and 16-lane segments).
+bool packable(const DevProblem& P)
+{
+    return (P.dyn == D4ORM_DYN_HOLO2D || P.dyn == D4ORM_DYN_HOLO3D) && P.n >= 5 && P.n <= 16;
+}
+
+// Autotuner bucket of a packable problem: dynamics x lane segment.
+int pack_bucket(const DevProblem& P) { return (P.dyn == D4ORM_DYN_HOLO3D ? 2 : 0) + (P.n > 8 ? 1 : 0); }
+
 }  // namespace
 
 struct d4orm_batch {
@@ -40,6 +50,9 @@ struct d4orm_batch {
     bool obstacles = false;            // any problem has obstacles: the kernel variant with the penalty
     float tuned_ms[3] = {-1.f, -1.f, -1.f};   // best pilot per CTA width
     int ctas_per_sm = 0;
+    // packing pilots: summed per-problem device time (ns) of each bucket
+    // (2D/3D holonomic x 5..8 / 9..16 robots), one robot vs two per lane
+    long long pack_ns[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
     // every pilot of the autotuner: CTA width, resident CTAs per SM, ms
     std::vector<int> tune_width, tune_occ;
     std::vector<float> tune_ms;
@@ -78,12 +91,15 @@ void batch_free(d4orm_batch* B)
 // One timed run of the persistent kernel over the whole batch with a short
 // schedule (2 steps, 1 iteration) at `threads` per CTA and `occ` CTAs per
 // SM (<= the resident maximum), for the autotuner.
-d4orm_status pilot_ms(d4orm_batch* B, int threads, int occ, float* ms)
+d4orm_status pilot_ms(d4orm_batch* B, int threads, int occ, float* ms, bool upload = false,
+                      bool read_results = false)
 {
     if (occ <= 0) {
         *ms = -1.f;
         return D4ORM_OK;
     }
+    if (upload)
+        B_CUDA(cudaMemcpy(B->d_insts, B->h_insts, sizeof(BatchInstance) * B->count, cudaMemcpyHostToDevice));
     const int grid = std::min(B->count, B->sms * occ);
     BatchConsts P = B->C;
     P.deadline_ns = 0;
@@ -107,6 +123,8 @@ d4orm_status pilot_ms(d4orm_batch* B, int threads, int occ, float* ms)
     }
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    if (e == cudaSuccess && read_results)
+        e = cudaMemcpy(B->h_results, B->d_results, sizeof(BatchResult) * B->count, cudaMemcpyDeviceToHost);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamDestroy(st);
@@ -207,6 +225,7 @@ d4orm_status d4orm_batch_create(d4orm_problem* const* problems, int count, const
         B->h_insts[b].du1 = B->d_work + 2 * total + off;
         B->h_insts[b].u_out = B->h_insts[b].tau_u;  // replaced by the caller's buffers at solve time
         B->h_insts[b].du_init = nullptr;
+        B->h_insts[b].paired = 0;
         off += nc;
     }
     // longest-first order: cost ~ samples x lanes x steps (+ the noise sum)
@@ -273,6 +292,32 @@ d4orm_status d4orm_batch_create(d4orm_problem* const* problems, int count, const
     B->threads = best;
     B->ctas_per_sm = occ;
     B->grid = std::min(count, B->sms * occ);
+
+    // robot-lane packing, per bucket (dynamics x lane segment) of the
+    // packable problems: at the chosen launch shape, one pilot with one robot
+    // per lane and one with two, compared by the problems' own device times
+    bool any_packable = false;
+    for (int b = 0; b < count; ++b) any_packable = any_packable || packable(B->h_probs[b]);
+    if (autotune && any_packable) {
+        for (int mode = 0; mode < 2; ++mode) {
+            for (int b = 0; b < count; ++b) B->h_insts[b].paired = mode;
+            float ms = -1.f;
+            s = pilot_ms(B, B->threads, B->ctas_per_sm, &ms, true, true);
+            if (s != D4ORM_OK) return fail_cleanup(s);
+            for (int b = 0; b < count; ++b)
+                if (packable(B->h_probs[b])) B->pack_ns[pack_bucket(B->h_probs[b])][mode] += B->h_results[b].ns_total;
+        }
+        for (int b = 0; b < count; ++b) {
+            const DevProblem& P = B->h_probs[b];
+            const int k = packable(P) ? pack_bucket(P) : -1;
+            B->h_insts[b].paired = k >= 0 && B->pack_ns[k][1] < B->pack_ns[k][0] ? 1 : 0;
+        }
+    } else {
+        // default: two robots per lane wherever the kernel has that rollout
+        for (int b = 0; b < count; ++b) B->h_insts[b].paired = packable(B->h_probs[b]) ? 1 : 0;
+    }
+    e = cudaMemcpy(B->d_insts, B->h_insts, sizeof(BatchInstance) * count, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail_cleanup(set_cuda_error(e, "batch upload"));
     *out = B;
     return D4ORM_OK;
 }
@@ -306,6 +351,30 @@ d4orm_status d4orm_batch_tuning(const d4orm_batch* B, int capacity, int* count, 
         if (ctas_per_sm) ctas_per_sm[i] = B->tune_occ[i];
         if (pilot_ms) pilot_ms[i] = B->tune_ms[i];
     }
+    return D4ORM_OK;
+}
+
+d4orm_status d4orm_batch_set_packing(d4orm_batch* B, int mode)
+{
+    if (!B) return set_error(D4ORM_ERR_INVALID_ARG, "null batch");
+    if (mode != D4ORM_PACK_SINGLE && mode != D4ORM_PACK_PAIRED)
+        return set_error(D4ORM_ERR_INVALID_ARG, "packing mode must be D4ORM_PACK_SINGLE or D4ORM_PACK_PAIRED");
+    // the staging buffer is copied to the device by the next solve's graph;
+    // wait for a replay that may still read it
+    B_CUDA(cudaDeviceSynchronize());
+    for (int b = 0; b < B->count; ++b)
+        B->h_insts[b].paired = mode == D4ORM_PACK_PAIRED && packable(B->h_probs[b]) ? 1 : 0;
+    return D4ORM_OK;
+}
+
+d4orm_status d4orm_batch_packing(const d4orm_batch* B, int capacity, int* paired, long long* bucket_ns)
+{
+    if (!B) return set_error(D4ORM_ERR_INVALID_ARG, "null batch");
+    if (paired)
+        for (int b = 0; b < B->count && b < capacity; ++b) paired[b] = B->h_insts[b].paired;
+    if (bucket_ns)
+        for (int k = 0; k < 4; ++k)
+            for (int m = 0; m < 2; ++m) bucket_ns[2 * k + m] = B->pack_ns[k][m];
     return D4ORM_OK;
 }
 

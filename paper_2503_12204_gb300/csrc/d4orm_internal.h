@@ -82,6 +82,7 @@ struct BatchInstance {
     float* du1;            // deformation pong
     float* u_out;          // caller's output plan
     const float* du_init;  // nullable warm-start deformation at start_step
+    int paired;            // rollouts with two robots per lane (5..16 robots only)
 };
 
 struct BatchConsts {

@@ -32,20 +32,8 @@ __device__ __forceinline__ f2 f2_pack(float lo, float hi)
     asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
     return r;
 }
-__device__ __forceinline__ float f2_lo(f2 v)
-{
-    float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-    (void)hi;
-    return lo;
-}
-__device__ __forceinline__ float f2_hi(f2 v)
-{
-    float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-    (void)lo;
-    return hi;
-}
+__device__ __forceinline__ float f2_lo(f2 v) { return __uint_as_float((unsigned)v); }
+__device__ __forceinline__ float f2_hi(f2 v) { return __uint_as_float((unsigned)(v >> 32)); }
 __device__ __forceinline__ f2 f2_sub(f2 a, f2 b)
 {
     f2 r;

@@ -25,10 +25,13 @@
 
 #include "d4orm_internal.h"
 #include "d4orm_kernels.cuh"
+#include "d4orm_paired.cuh"
 
 namespace d4orm {
 
-template <int DYN, int SEG, bool OBS>
+// PAIRED: the samples' rollouts use two robots per lane (L = SEG/2 lanes
+// per sample, f32x2 arithmetic), otherwise one robot per lane.
+template <int DYN, int SEG, bool OBS, bool PAIRED>
 __device__ __noinline__ void batched_instance(const DevProblem& P, const BatchInstance& I, const BatchConsts& C,
                                                  const float4* __restrict__ sched, int b, float* sM, float* sFit,
                                                  float2* sList, float4* sRed, float* sh, int* scan, int* s_count,
@@ -89,12 +92,15 @@ __device__ __noinline__ void batched_instance(const DevProblem& P, const BatchIn
             // mean controls M = tau.u + c dU_i
             stage_mean<false>(sM, du[cur], tau, S.c, nctrl);  // written by this CTA: coherent loads
             __syncthreads();
-            // fitness of all N samples, 32/SEG per warp per pass
-            constexpr int SPW = 32 / SEG;
+            // fitness of all N samples, 32/SEG (paired: 32/(SEG/2)) per warp per pass
+            constexpr int LPS = PAIRED ? SEG / 2 : SEG;  // lanes per sample
+            constexpr int SPW = 32 / LPS;
             for (int base = 0; base < N; base += nw * SPW) {
-                const int j = base + warp * SPW + lane / SEG;
-                const float f = sample_fitness_segment<DYN, SEG, OBS>(P, S, sM, c3, j);
-                if ((lane & (SEG - 1)) == 0 && j < N) sFit[j] = f;
+                const int j = base + warp * SPW + lane / LPS;
+                float f;
+                if constexpr (PAIRED) f = sample_fitness_paired<DYN, LPS, OBS>(P, S, sM, c3, j);
+                else f = sample_fitness_segment<DYN, SEG, OBS>(P, S, sM, c3, j);
+                if ((lane & (LPS - 1)) == 0 && j < N) sFit[j] = f;
             }
             __syncthreads();
             // batch softmax + compaction (Sec. IV-C, Eq. (6))
@@ -178,18 +184,32 @@ __device__ __forceinline__ void batched_dispatch_seg(const DevProblem& P, const 
                                                      int* s_count, d4orm_verdict* s_verdict, BatchResult* results,
                                                      long long t_launch, int* s_stop)
 {
-#define D4_CASE(SEGV) batched_instance<DYN, SEGV, OBS>(P, I, C, sched, b, sM, sFit, sList, sRed, sh, scan, s_count, \
-                                                  s_verdict, results, t_launch, s_stop)
-    if (P.n <= 2) D4_CASE(2);
-    else if (P.n <= 4) D4_CASE(4);
-    else if (P.n <= 8) D4_CASE(8);
-    else if (P.n <= 16) D4_CASE(16);
-    else D4_CASE(32);
+#define D4_CASE(SEGV, PV) batched_instance<DYN, SEGV, OBS, PV>(P, I, C, sched, b, sM, sFit, sList, sRed, sh, scan, \
+                                                           s_count, s_verdict, results, t_launch, s_stop)
+    // robot-lane packing (I.paired, chosen per problem by the autotuner) is
+    // compiled for holonomic teams in the 8- and 16-lane segments (5..16
+    // robots): the only cases where both the integration and the pair tests
+    // pack into f32x2 and the paired rollout fits the register budget
+    constexpr bool kPack = DYN == D4ORM_DYN_HOLO2D || DYN == D4ORM_DYN_HOLO3D;
+    const bool pack = kPack && I.paired;
+    if (P.n <= 2) D4_CASE(2, false);
+    else if (P.n <= 4) D4_CASE(4, false);
+    else if (P.n <= 8) {
+        if constexpr (kPack) {
+            if (pack) D4_CASE(8, true);
+            else D4_CASE(8, false);
+        } else D4_CASE(8, false);
+    } else if (P.n <= 16) {
+        if constexpr (kPack) {
+            if (pack) D4_CASE(16, true);
+            else D4_CASE(16, false);
+        } else D4_CASE(16, false);
+    } else D4_CASE(32, false);
 #undef D4_CASE
 }
 
 template <bool OBS>
-__global__ void __launch_bounds__(kBatchMaxThreads, 2)
+__global__ void __launch_bounds__(kBatchMaxThreads, 1)
 k_batched_solve(const DevProblem* __restrict__ probs, const BatchInstance* __restrict__ insts,
                 const int* __restrict__ order, const float4* __restrict__ sched, const BatchConsts C, int* queue,
                 BatchResult* results)

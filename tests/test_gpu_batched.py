@@ -85,6 +85,93 @@ def test_batched_matches_single_solves(torch, g, oracle_lib, autotune):
     g.d4orm_batch_destroy(batch)
 
 
+@pytest.mark.parametrize("obstacles", [False, True])
+def test_batched_packing_matches_single_solves(torch, g, oracle_lib, obstacles):
+    """Two robots per lane in the batched kernel (2D/3D holonomic teams of
+    5..16 robots, both lane segments, plus a unicycle team and a 3-robot
+    team that keep one robot per lane); the packing flags follow the rule.
+    One denoising step from the same random deformation (warm start at step
+    1) evaluates every sample on the same mean controls, so the batched
+    solve with one robot per lane, with two, and the single-problem solve
+    differ only in the order of float sums: plans agree to 1e-4 of their
+    scale.  Over whole solves (5 steps x 2 iterations) those differences
+    reach the later steps' mean controls in the last bit, which can flip the
+    indicator of a sample sitting on a collision or obstacle boundary.
+    Without obstacles such samples are rare and the plans still agree to
+    1e-3; with obstacles (placed on the start-goal segments, so that many
+    samples graze them) the paired plans are re-judged by the oracle."""
+    rng = np.random.default_rng(21)
+    cases = [(scenarios.HOLO2D, 5), (scenarios.HOLO2D, 8), (scenarios.HOLO2D, 11), (scenarios.HOLO2D, 16),
+             (scenarios.HOLO3D, 6), (scenarios.HOLO3D, 9), (scenarios.HOLO3D, 16), (scenarios.UNICYCLE, 12),
+             (scenarios.HOLO2D, 3)]
+    insts = [round_instance(scenarios.box_instance(rng, dyn, n, 30 + 7 * b, 256, K=5))
+             for b, (dyn, n) in enumerate(cases)]
+    if obstacles:
+        insts = [add_obstacles(i, 1 + (5 * b) % 9, seed=b) if b % 2 == 1 else i for b, i in enumerate(insts)]
+    probs = [g.Problem(i) for i in insts]
+    params = g.Params(n_samples=256, n_steps=5, seed=4, instance_tag=60)
+    du0 = [torch.tensor(scenarios.random_deformation(rng, i), dtype=torch.float32, device="cuda") for i in insts]
+    one, full = g.Budget(max_iters=1, start_step=1), g.Budget(max_iters=2)
+    batch = g.d4orm_batch_create([p.handle for p in probs], params, autotune=False)
+    want = [1 if dyn in (scenarios.HOLO2D, scenarios.HOLO3D) and 5 <= n <= 16 else 0 for dyn, n in cases]
+    plans = {}
+    for mode in (g.PACK_PAIRED, g.PACK_SINGLE):
+        g.d4orm_batch_set_packing(batch, mode)
+        flags = g.d4orm_batch_packing(batch, len(insts))["paired"]
+        assert flags == (want if mode == g.PACK_PAIRED else [0] * len(insts))
+        outs1 = [torch.zeros((i.T, i.n, i.dims[1]), device="cuda") for i in insts]
+        g.d4orm_batch_solve(batch, one, outs1, du_init_devs=du0)
+        outs2 = [torch.zeros((i.T, i.n, i.dims[1]), device="cuda") for i in insts]
+        res = g.d4orm_batch_solve(batch, full, outs2)
+        torch.cuda.synchronize()
+        assert all(r["iters_run"] == 2 for r in res)
+        plans[mode] = ([o.cpu().numpy() for o in outs1], [o.cpu().numpy() for o in outs2], res)
+    for b, (inst, p) in enumerate(zip(insts, probs)):
+        single = g.Params(n_samples=256, n_steps=5, seed=4, instance_tag=60 + b)
+        u1 = torch.zeros((inst.T, inst.n, inst.dims[1]), device="cuda")
+        g.d4orm_solve(p.handle, single, one, u1, du_init_dev=du0[b])
+        u2 = torch.zeros_like(u1)
+        r2 = g.d4orm_solve(p.handle, single, full, u2)
+        s1, s2 = u1.cpu().numpy(), u2.cpu().numpy()
+        for mode in (g.PACK_PAIRED, g.PACK_SINGLE):
+            a1, a2 = plans[mode][0][b], plans[mode][1][b]
+            scale = max(np.abs(s1).max(), 1e-3)
+            assert np.abs(a1 - s1).max() <= 1e-4 * scale, (mode, b, np.abs(a1 - s1).max(), scale)
+            if not obstacles:
+                scale = max(np.abs(s2).max(), 1e-3)
+                assert np.abs(a2 - s2).max() <= 1e-3 * scale, (mode, b, np.abs(a2 - s2).max(), scale)
+        a2 = plans[g.PACK_PAIRED][1][b]
+        st = oracle_lib.rollout(oracle_problem(oracle_lib, inst), a2.astype(np.float64))
+        vo = oracle_lib.verdict(oracle_problem(oracle_lib, inst), inst.w_safe, st)
+        if abs(vo["min_pair_dist"] - 2 * inst.radius) > DELTA and (not obstacles or
+                                                                   obstacle_safety_gap(inst, st) > DELTA):
+            assert plans[g.PACK_PAIRED][2][b]["verdict"]["collision_free"] == vo["collision_free"]
+            if not obstacles:
+                assert vo["collision_free"] == r2["verdict"]["collision_free"]
+    with pytest.raises(g.D4ormError):
+        g.d4orm_batch_set_packing(batch, 2)
+    g.d4orm_batch_destroy(batch)
+
+
+def test_batched_packing_autotune_rule(torch, g):
+    """The autotuner's packing pilots: every bucket with packable problems
+    has both sums measured, and each problem is paired exactly when its
+    bucket's paired sum is the smaller."""
+    insts = _mixed(40, seed=17, N=256, K=4)
+    probs = [g.Problem(i) for i in insts]
+    params = g.Params(n_samples=256, n_steps=4, seed=1, instance_tag=300)
+    batch = g.d4orm_batch_create([p.handle for p in probs], params, autotune=True)
+    pk = g.d4orm_batch_packing(batch, len(insts))
+    for b, inst in enumerate(insts):
+        if inst.dyn in (scenarios.HOLO2D, scenarios.HOLO3D) and 5 <= inst.n <= 16:
+            single, paired = pk["bucket_ns"][(inst.dyn, "5-8" if inst.n <= 8 else "9-16")]
+            assert single > 0 and paired > 0
+            assert pk["paired"][b] == (1 if paired < single else 0)
+        else:
+            assert pk["paired"][b] == 0
+    g.d4orm_batch_destroy(batch)
+
+
 def test_batched_with_obstacles_matches_single_solves(torch, g, oracle_lib):
     """Ragged batch where every other problem carries 1..16 obstacles: the
     persistent kernel evaluates the same obstacle term as the single path."""

@@ -344,12 +344,15 @@ def test_sample_fitness_entry_point(torch, g, oracle_lib, dyn, n, T, N, kernel):
         g.d4orm_sample_fitness(prob.handle, p, 0, 0, dev(torch, ub), dev(torch, du), f1)
 
 
-@pytest.mark.parametrize("dyn,n,T,N", [(0, 4, 50, 256), (2, 8, 100, 700), (1, 16, 37, 300), (3, 32, 9, 40)])
-def test_rollout_kernels_agree(torch, g, dyn, n, T, N):
+@pytest.mark.parametrize("dyn,n,T,N,m", [(0, 4, 50, 256, 0), (2, 8, 100, 700, 0), (1, 16, 37, 300, 0),
+                                         (3, 32, 9, 40, 0), (0, 16, 51, 256, 7), (1, 11, 30, 200, 16)])
+def test_rollout_kernels_agree(torch, g, dyn, n, T, N, m):
     """The register, pipeline and paired kernels evaluate the same samples
     with the same arithmetic; only the order of the fitness summation
-    differs."""
+    differs (m > 0: with obstacles on the start-goal segments)."""
     inst = small_instance(dyn, n, T, N, seed=13, K=20)
+    if m:
+        inst = add_obstacles(inst, m, seed=n + T)
     rng = np.random.default_rng(2)
     ub = dev(torch, scenarios.random_controls(rng, inst, 0.5))
     du = dev(torch, scenarios.random_deformation(rng, inst))
