@@ -573,7 +573,7 @@ def run_ours(args):
     u_out = torch.zeros((inst.T, inst.n, d_u), device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     rollouts_per_step = inst.N * inst.K * inst.iters
-    launches_per_step = inst.iters * (4 * inst.K + 1)
+    launches_per_step = inst.iters * (3 * inst.K + 1)
 
     for _ in range(args.warmup):
         g.d4orm_solve(prob.handle, params, budget, u_out, stream=stream)
@@ -665,8 +665,8 @@ def run_ours(args):
                      "flops_per_launch": flops, "launch_ms": k2_ms,
                      "timing": f"{GRAPH_REPS} launches replayed from one CUDA graph, events on the stream",
                      "eager_event_launch_ms": float(kms[:, 0].mean())},
-        "kernel_share": {"rollout_fitness": share[0], "softmax_weights": share[1], "weighted_sum": share[2],
-                         "finalize": share[3], "eager_step_ms": step_ms},
+        "kernel_share": {"rollout_fitness": share[0], "softmax_weights": share[1], "weighted_mean": share[2],
+                         "eager_step_ms": step_ms},
         "verdict": results[-1]["verdict"],
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

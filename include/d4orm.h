@@ -244,8 +244,8 @@ d4orm_status d4orm_sample_fitness(d4orm_problem *problem, const d4orm_params *pa
 
 /* d4orm_denoise_step with a CUDA event recorded on `stream` between its
  * kernels; synchronises and writes the device time of each kernel, in ms,
- * to kernel_ms_host[4]: {rollout+fitness, softmax weights, weighted noise
- * sum, finalize}.  A ~200 us sleep kernel runs first so that the events
+ * to kernel_ms_host[3]: {rollout+fitness, softmax weights, weighted noise
+ * sum with the Eq. (13) update}.  A ~200 us sleep kernel runs first so that the events
  * bracket device time, not host submission.
  * Results are identical to d4orm_denoise_step. */
 d4orm_status d4orm_denoise_step_timed(d4orm_problem *problem, const d4orm_params *params, int iter, int step_i,
@@ -259,15 +259,14 @@ d4orm_status d4orm_denoise_step_timed(d4orm_problem *problem, const d4orm_params
  * device memory in its own pool up front and forbids allocations by
  * libraries.  It computes exactly what d4orm_denoise_step computes (same
  * kernels, same launch shapes), but its scratch (weights, fitness when
- * fitness_dev is NULL, per-chunk partial sums) lives in a fixed 2 MiB array
+ * fitness_dev is NULL, batch statistics) lives in a fixed 2 MiB array
  * inside the library's device image instead of the problem's workspace, so
  * the call allocates nothing: no cudaMalloc, no cudaFree, no allocating
  * library routine.  (d4orm_problem_create allocates no device memory.)
  * The caller still passes every input and output buffer.
- *  - Limits: n_samples <= D4ORM_NOALLOC_MAX_SAMPLES, and the problem's
- *    scratch must fit in D4ORM_NOALLOC_SCRATCH_FLOATS floats (every problem
- *    create accepts does on GPUs with up to 152 SMs); beyond either the call
- *    returns D4ORM_ERR_UNSUPPORTED before launching anything.
+ *  - Limits: n_samples <= D4ORM_NOALLOC_MAX_SAMPLES (the scratch, 3 floats
+ *    per sample plus 64, then fits in D4ORM_NOALLOC_SCRATCH_FLOATS); beyond
+ *    it the call returns D4ORM_ERR_UNSUPPORTED before launching anything.
  *  - Each call looks up the array's device address with the calling
  *    thread's device current (the host-side name of the array is only a
  *    stand-in) and sets the problem's rollout-kernel attributes; the first

@@ -339,9 +339,9 @@ def d4orm_denoise_step(handle, params: Params, iter: int, step_i: int, u_base_de
 def d4orm_denoise_step_timed(handle, params: Params, iter: int, step_i: int, u_base_dev, du_in_dev, du_out_dev,
                              fitness_dev=None, stream=None) -> list[float]:
     """Same as d4orm_denoise_step; returns the per-kernel device times [ms]
-    (rollout+fitness, softmax weights, weighted noise sum, finalize)."""
+    (rollout+fitness, softmax weights, weighted noise sum with the update)."""
     pc = params.c()
-    ms = (ctypes.c_float * 4)()
+    ms = (ctypes.c_float * 3)()
     _check(lib.d4orm_denoise_step_timed(handle, ctypes.byref(pc), iter, step_i, _ptr(u_base_dev), _ptr(du_in_dev),
                                         _ptr(du_out_dev), _ptr(fitness_dev), ms, _stream(stream)))
     return list(ms)

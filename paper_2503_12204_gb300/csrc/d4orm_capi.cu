@@ -84,8 +84,6 @@ struct d4orm_problem {
     float2* d_list = nullptr;    // [N] (weight, sample index) of the samples that carry weight
     int* d_count = nullptr;      // list length
     float* d_stats = nullptr;    // [4]
-    float* d_partial = nullptr;  // [chunks][n*Q][4]
-    size_t partial_cap = 0;      // floats
     float* d_tau_u = nullptr;    // tau.u  [T][n][d_u]
     float* d_du[2] = {nullptr, nullptr};
     d4orm_verdict* d_verdicts = nullptr;  // [1 + D4ORM_MAX_ITERS]: slot 0 = latest, 1+it = history
@@ -172,19 +170,6 @@ d4orm_status ensure_workspace(d4orm_problem* P, int N)
         }
         P->ws_N = N;
     }
-    const SumSplit sp = plan_weighted_sum(P->dp, N, P->sm_count);
-    const size_t need = (size_t)sp.chunks * P->n * P->dp.Q * 4;
-    if (need > P->partial_cap) {
-        free_graphs(P);
-        cudaFree(P->d_partial);
-        P->d_partial = nullptr;
-        if (cudaMalloc(&P->d_partial, need * sizeof(float)) != cudaSuccess) {
-            cudaGetLastError();
-            P->partial_cap = 0;
-            return fail(D4ORM_ERR_OOM, "partial-sum workspace allocation failed");
-        }
-        P->partial_cap = need;
-    }
     return D4ORM_OK;
 }
 
@@ -252,12 +237,10 @@ DevStep step_consts(const d4orm_params* p, const std::vector<double>& abar, int 
 d4orm_status enqueue_step(d4orm_problem* P, const DevStep& S, const float* u_base, const float* du_in, float* du_out,
                           float* fitness, const int* it_dev, cudaStream_t st)
 {
-    const SumSplit sp = plan_weighted_sum(P->dp, S.N, P->sm_count);
     float* fit = fitness ? fitness : P->d_fit;
     D4_CUDA(launch_rollout_fitness(P->dp, S, u_base, du_in, fit, it_dev, P->sm_count, P->rollout_kernel, st));
     D4_CUDA(launch_softmax_weights(fit, S.N, S.inv_lambda, P->d_list, P->d_count, P->d_stats, st));
-    D4_CUDA(launch_weighted_sum(P->dp, S, P->d_list, P->d_count, sp, P->d_partial, it_dev, st));
-    D4_CUDA(launch_finalize(P->dp, S, P->d_partial, sp, du_in, du_out, st));
+    D4_CUDA(launch_weighted_mean(P->dp, S, P->d_list, P->d_count, du_in, du_out, it_dev, P->sm_count, st));
     return D4ORM_OK;
 }
 
@@ -477,7 +460,6 @@ void d4orm_problem_destroy(d4orm_problem* P)
         cudaFree(P->d_list);
         cudaFree(P->d_count);
         cudaFree(P->d_stats);
-        cudaFree(P->d_partial);
         cudaFree(P->d_tau_u);
         cudaFree(P->d_du[0]);
         cudaFree(P->d_du[1]);
@@ -690,10 +672,9 @@ d4orm_status d4orm_denoise_step_timed(d4orm_problem* P, const d4orm_params* para
     schedule(params, abar);
     const DevStep S = step_consts(params, abar, iter, step_i);
     cudaStream_t st = (cudaStream_t)stream;
-    const SumSplit sp = plan_weighted_sum(P->dp, S.N, P->sm_count);
     float* fit = fitness_dev ? fitness_dev : P->d_fit;
-    cudaEvent_t ev[5];
-    for (int k = 0; k < 5; ++k) D4_CUDA(cudaEventCreate(&ev[k]));
+    cudaEvent_t ev[4];
+    for (int k = 0; k < 4; ++k) D4_CUDA(cudaEventCreate(&ev[k]));
     // a short sleep first, so that every kernel below is already submitted
     // when the first event fires: the events then bracket device time only
     cudaError_t e = launch_hold(200, st);
@@ -703,13 +684,12 @@ d4orm_status d4orm_denoise_step_timed(d4orm_problem* P, const d4orm_params* para
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
     if (e == cudaSuccess) e = launch_softmax_weights(fit, S.N, S.inv_lambda, P->d_list, P->d_count, P->d_stats, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
-    if (e == cudaSuccess) e = launch_weighted_sum(P->dp, S, P->d_list, P->d_count, sp, P->d_partial, nullptr, st);
+    if (e == cudaSuccess)
+        e = launch_weighted_mean(P->dp, S, P->d_list, P->d_count, du_in_dev, du_out_dev, nullptr, P->sm_count, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3], st);
-    if (e == cudaSuccess) e = launch_finalize(P->dp, S, P->d_partial, sp, du_in_dev, du_out_dev, st);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[4], st);
-    if (e == cudaSuccess) e = cudaEventSynchronize(ev[4]);
-    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventElapsedTime(&kernel_ms_host[k], ev[k], ev[k + 1]);
-    for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventElapsedTime(&kernel_ms_host[k], ev[k], ev[k + 1]);
+    for (int k = 0; k < 4; ++k) cudaEventDestroy(ev[k]);
     if (e != cudaSuccess) return cuda_fail(e, "d4orm_denoise_step_timed");
     return D4ORM_OK;
 }

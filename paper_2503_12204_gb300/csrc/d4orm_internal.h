@@ -9,14 +9,6 @@
 
 namespace d4orm {
 
-// Split of the weighted noise sum over samples: `chunks` partial sums of
-// `chunk` samples each (chunk a multiple of 8).
-struct SumSplit {
-    int chunks;
-    int chunk;
-};
-SumSplit plan_weighted_sum(const DevProblem& P, int N, int sm_count);
-
 // Kernel attributes K2 needs for problem P (call outside stream capture).
 cudaError_t prepare_rollout_fitness(const DevProblem& P);
 cudaError_t prepare_rollout_fitness_pipe(const DevProblem& P);
@@ -48,13 +40,10 @@ size_t rollout_fitness_pipe_smem(const DevProblem& P);
 cudaError_t launch_softmax_weights(const float* fitness, int N, float inv_lambda, float2* list, int* count,
                                    float* stats, cudaStream_t st);
 
-// K3b: partial[c][n*Q][4] = sum of w_j eps_j over the list entries dealt to chunk c.
-cudaError_t launch_weighted_sum(const DevProblem& P, const DevStep& S, const float2* list, const int* count,
-                                SumSplit split, float* partial, const int* it_dev, cudaStream_t st);
-
-// K3c: du_out = g (c du_in + sigma sum_c partial[c])  (Eq. (13)).
-cudaError_t launch_finalize(const DevProblem& P, const DevStep& S, const float* partial, SumSplit split,
-                            const float* du_in, float* du_out, cudaStream_t st);
+// K3b: du_out = g (c du_in + sigma sum_j w_j eps_j) over the listed samples,
+// eps regenerated (Eq. (12) noise, Eq. (13) update), in one pass.
+cudaError_t launch_weighted_mean(const DevProblem& P, const DevStep& S, const float2* list, const int* count,
+                                 const float* du_in, float* du_out, const int* it_dev, int sm_count, cudaStream_t st);
 
 // K4: u_out = clip(u_base + du0) (du0 nullable), rollout, verdict.
 // states (nullable) [T+1][n][d_x]; verdict (nullable) device struct;

@@ -5,14 +5,15 @@
 // latency bound, and host applications that reserve all device memory up
 // front in their own pool and forbid allocations by plug-in libraries.
 // d4orm_denoise_step gets its scratch (fitness, the compacted weight list,
-// per-chunk partial sums) from the problem's workspace, which it allocates on first use; this
+// the batch statistics) from the problem's workspace, which it allocates on
+// first use; this
 // variant takes the same scratch from a fixed array that is part of the
 // library's device image, so it never allocates.  The problem handle itself
 // holds no device memory (d4orm_problem_create allocates none).
 //
 // The array is shared by every call on a device and keeps the last call's
 // contents.  Nothing in it needs to start at zero: each step writes every
-// fitness, list, count and partial-sum entry it later reads.  Calls whose work
+// fitness, list and count entry it later reads.  Calls whose work
 // overlaps on the GPU (other streams, or other host threads) race on it.
 #include <mutex>
 
@@ -91,25 +92,22 @@ extern "C" d4orm_status d4orm_denoise_step_noalloc(const d4orm_problem* problem,
     // kernel attribute of the current context: applied on every call, so a
     // re-created context gets it too)
     if ((e = prepare_rollout_fitness(P)) != cudaSuccess) return set_cuda_error(e, "cudaFuncSetAttribute");
-    const SumSplit split = plan_weighted_sum(P, N, ds->sm_count);
     const size_t n_w = 2 * pad64((size_t)N), n_fit = pad64((size_t)N), n_stats = 64;
-    const size_t n_partial = (size_t)split.chunks * P.n * P.Q * 4;
-    if (n_w + n_fit + n_stats + n_partial > kScratchFloats)
+    if (n_w + n_fit + n_stats > kScratchFloats)
         return set_error(D4ORM_ERR_UNSUPPORTED, "d4orm_denoise_step_noalloc: problem needs more scratch than "
                                                 "D4ORM_NOALLOC_SCRATCH_FLOATS");
     float2* list = reinterpret_cast<float2*>(ds->scratch);
     float* fit = fitness_dev ? fitness_dev : ds->scratch + n_w;
     float* stats = ds->scratch + n_w + n_fit;
     int* count = reinterpret_cast<int*>(stats + 8);
-    float* partial = stats + n_stats;
 
     const DevStep S = make_step_consts(params, iter, step_i);
     cudaStream_t st = (cudaStream_t)stream;
     if ((e = launch_rollout_fitness(P, S, u_base_dev, du_in_dev, fit, nullptr, ds->sm_count,
                                      rollout_kernel_choice(problem), st)) != cudaSuccess ||
         (e = launch_softmax_weights(fit, N, S.inv_lambda, list, count, stats, st)) != cudaSuccess ||
-        (e = launch_weighted_sum(P, S, list, count, split, partial, nullptr, st)) != cudaSuccess ||
-        (e = launch_finalize(P, S, partial, split, du_in_dev, du_out_dev, st)) != cudaSuccess)
+        (e = launch_weighted_mean(P, S, list, count, du_in_dev, du_out_dev, nullptr, ds->sm_count, st)) !=
+            cudaSuccess)
         return set_cuda_error(e, "d4orm_denoise_step_noalloc launch");
     return D4ORM_OK;
 }

@@ -344,6 +344,34 @@ def test_sample_fitness_entry_point(torch, g, oracle_lib, dyn, n, T, N, kernel):
         g.d4orm_sample_fitness(prob.handle, p, 0, 0, dev(torch, ub), dev(torch, du), f1)
 
 
+def test_timed_and_noalloc_steps_equal_the_step(torch, g):
+    """d4orm_denoise_step_timed and d4orm_denoise_step_noalloc run the same
+    kernels with the same launch shapes as d4orm_denoise_step: identical
+    fitness and update bits; the timed call reports three positive kernel
+    times (rollout + fitness, softmax weights, weighted mean)."""
+    inst = small_instance(1, 12, 41, 1500, seed=6, K=20)
+    rng = np.random.default_rng(8)
+    ub = dev(torch, scenarios.random_controls(rng, inst, 0.5))
+    du = dev(torch, scenarios.random_deformation(rng, inst))
+    prob = g.Problem(inst)
+    p = gpu_params(g, inst)
+    outs, fits = [], []
+    for call in ("step", "timed", "noalloc"):
+        o, f = torch.zeros_like(du), torch.zeros(inst.N, device="cuda")
+        if call == "step":
+            g.d4orm_denoise_step(prob.handle, p, 1, 13, ub, du, o, f)
+        elif call == "timed":
+            ms = g.d4orm_denoise_step_timed(prob.handle, p, 1, 13, ub, du, o, f)
+            assert len(ms) == 3 and all(t > 0 for t in ms)
+        else:
+            g.d4orm_denoise_step_noalloc(prob.handle, p, 1, 13, ub, du, o, f)
+        torch.cuda.synchronize()
+        outs.append(o)
+        fits.append(f)
+    for o, f in zip(outs[1:], fits[1:]):
+        assert torch.equal(f, fits[0]) and torch.equal(o, outs[0])
+
+
 @pytest.mark.parametrize("dyn,n,T,N,m", [(0, 4, 50, 256, 0), (2, 8, 100, 700, 0), (1, 16, 37, 300, 0),
                                          (3, 32, 9, 40, 0), (0, 16, 51, 256, 7), (1, 11, 30, 200, 16)])
 def test_rollout_kernels_agree(torch, g, dyn, n, T, N, m):
