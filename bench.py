@@ -339,10 +339,10 @@ def packing_summary(g, batch, count):
     """Problems rolled out two robots per lane and the autotuner's packing
     pilots (summed device ms per bucket, one robot vs two per lane)."""
     pk = g.d4orm_batch_packing(batch, count)
-    names = {g.HOLO2D: "holo2d", g.HOLO3D: "holo3d"}
+    names = {g.HOLO2D: "holo2d", g.HOLO3D: "holo3d", g.UNICYCLE: "unicycle", g.DIFFDRIVE4: "diffdrive4"}
     return {"paired_problems": sum(pk["paired"]),
             "pilot_ms_single_paired": {f"{names[d]}_{r}": [round(s * 1e-6, 3), round(q * 1e-6, 3)]
-                                       for (d, r), (s, q) in pk["bucket_ns"].items()}}
+                                       for (d, r), (s, q) in pk["bucket_ns"].items() if s or q}}
 
 
 def run_batched(args, torch, g, world, rank):

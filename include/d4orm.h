@@ -366,10 +366,11 @@ d4orm_status d4orm_batch_tuning(const d4orm_batch *batch, int capacity, int *cou
                                 int *ctas_per_sm, float *pilot_ms);
 
 /* Robot-lane packing of the batched solver's sample rollouts.  SINGLE: one
- * robot per lane.  PAIRED: two robots per lane, their dynamics and pair
- * tests issued as packed f32x2 arithmetic; the kernel has this rollout for
- * 2D/3D holonomic teams of 5..16 robots, and other problems keep one robot
- * per lane.  Both give the same rewards up to the order of float sums. */
+ * robot per lane.  PAIRED: two robots per lane, their pair tests and goal
+ * terms (and, for holonomic teams, their integration) issued as packed
+ * f32x2 arithmetic; the kernel has this rollout for teams of 5..16 robots,
+ * and other problems keep one robot per lane.  Both give the same rewards
+ * up to the order of float sums. */
 enum { D4ORM_PACK_SINGLE = 0, D4ORM_PACK_PAIRED = 1 };
 
 /* Set the packing of every problem of the batch (overrides the
@@ -379,10 +380,11 @@ enum { D4ORM_PACK_SINGLE = 0, D4ORM_PACK_PAIRED = 1 };
 d4orm_status d4orm_batch_set_packing(d4orm_batch *batch, int mode);
 
 /* The packing each problem uses: paired[b] = 1 for two robots per lane (at
- * most `capacity` entries, nullable).  bucket_ns (nullable, 8 entries): the
- * autotuner's packing pilots, summed device ns of the problems of each
- * bucket (2D holonomic 5..8 robots, 2D 9..16, 3D 5..8, 3D 9..16) with one
- * and then two robots per lane; zeros without autotuning.  With
+ * most `capacity` entries, nullable).  bucket_ns (nullable, 16 entries):
+ * the autotuner's packing pilots, summed device ns of the problems of each
+ * bucket with one and then two robots per lane, buckets in the order
+ * (dynamics d, 5..8 robots), (d, 9..16 robots) for d = D4ORM_DYN_HOLO2D,
+ * HOLO3D, UNICYCLE, DIFFDRIVE4; zeros without autotuning.  With
  * autotuning a bucket is packed when its paired sum is the smaller;
  * without it, every packable problem is. */
 d4orm_status d4orm_batch_packing(const d4orm_batch *batch, int capacity, int *paired, long long *bucket_ns);

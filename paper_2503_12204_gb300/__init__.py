@@ -454,7 +454,7 @@ def d4orm_batch_tuning(batch) -> list[dict]:
 
 def d4orm_batch_set_packing(batch, mode: int) -> None:
     """PACK_SINGLE or PACK_PAIRED for every problem (paired only where the
-    kernel has the two-robots-per-lane rollout)."""
+    kernel has the two-robots-per-lane rollout: teams of 5..16 robots)."""
     _check(lib.d4orm_batch_set_packing(batch, int(mode)))
 
 
@@ -462,11 +462,11 @@ def d4orm_batch_packing(batch, count: int) -> dict:
     """Per-problem packing (1 = two robots per lane) and the packing
     pilots' summed device ns per bucket: {(dyn, "5-8"|"9-16"): (single, paired)}."""
     paired = (ctypes.c_int * max(1, count))()
-    ns = (ctypes.c_longlong * 8)()
+    ns = (ctypes.c_longlong * 16)()
     _check(lib.d4orm_batch_packing(batch, count, paired, ns))
-    names = [(HOLO2D, "5-8"), (HOLO2D, "9-16"), (HOLO3D, "5-8"), (HOLO3D, "9-16")]
+    names = [(d, r) for d in (HOLO2D, HOLO3D, UNICYCLE, DIFFDRIVE4) for r in ("5-8", "9-16")]
     return dict(paired=[paired[b] for b in range(count)],
-                bucket_ns={names[k]: (ns[2 * k], ns[2 * k + 1]) for k in range(4)})
+                bucket_ns={names[k]: (ns[2 * k], ns[2 * k + 1]) for k in range(8)})
 
 
 def d4orm_batch_info(batch) -> dict:

@@ -17,15 +17,13 @@ namespace {
 
 int seg_of(int n) { return n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : 32; }
 
-// The batched kernel has a two-robots-per-lane rollout for holonomic teams
-// of 5..16 robots (8- and 16-lane segments).
-bool packable(const DevProblem& P)
-{
-    return (P.dyn == D4ORM_DYN_HOLO2D || P.dyn == D4ORM_DYN_HOLO3D) && P.n >= 5 && P.n <= 16;
-}
+// The batched kernel has a two-robots-per-lane rollout for teams of 5..16
+// robots (8- and 16-lane segments), every dynamics model.
+bool packable(const DevProblem& P) { return P.n >= 5 && P.n <= 16; }
 
 // Autotuner bucket of a packable problem: dynamics x lane segment.
-int pack_bucket(const DevProblem& P) { return (P.dyn == D4ORM_DYN_HOLO3D ? 2 : 0) + (P.n > 8 ? 1 : 0); }
+constexpr int kPackBuckets = 8;
+int pack_bucket(const DevProblem& P) { return 2 * P.dyn + (P.n > 8 ? 1 : 0); }
 
 }  // namespace
 
@@ -51,8 +49,8 @@ struct d4orm_batch {
     float tuned_ms[3] = {-1.f, -1.f, -1.f};   // best pilot per CTA width
     int ctas_per_sm = 0;
     // packing pilots: summed per-problem device time (ns) of each bucket
-    // (2D/3D holonomic x 5..8 / 9..16 robots), one robot vs two per lane
-    long long pack_ns[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    // (dynamics x 5..8 / 9..16 robots), one robot vs two per lane
+    long long pack_ns[kPackBuckets][2] = {};
     // every pilot of the autotuner: CTA width, resident CTAs per SM, ms
     std::vector<int> tune_width, tune_occ;
     std::vector<float> tune_ms;
@@ -373,7 +371,7 @@ d4orm_status d4orm_batch_packing(const d4orm_batch* B, int capacity, int* paired
     if (paired)
         for (int b = 0; b < B->count && b < capacity; ++b) paired[b] = B->h_insts[b].paired;
     if (bucket_ns)
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < kPackBuckets; ++k)
             for (int m = 0; m < 2; ++m) bucket_ns[2 * k + m] = B->pack_ns[k][m];
     return D4ORM_OK;
 }

@@ -187,23 +187,17 @@ __device__ __forceinline__ void batched_dispatch_seg(const DevProblem& P, const 
 #define D4_CASE(SEGV, PV) batched_instance<DYN, SEGV, OBS, PV>(P, I, C, sched, b, sM, sFit, sList, sRed, sh, scan, \
                                                            s_count, s_verdict, results, t_launch, s_stop)
     // robot-lane packing (I.paired, chosen per problem by the autotuner) is
-    // compiled for holonomic teams in the 8- and 16-lane segments (5..16
-    // robots): the only cases where both the integration and the pair tests
-    // pack into f32x2 and the paired rollout fits the register budget
-    constexpr bool kPack = DYN == D4ORM_DYN_HOLO2D || DYN == D4ORM_DYN_HOLO3D;
-    const bool pack = kPack && I.paired;
+    // compiled for the 8- and 16-lane segments (5..16 robots); holonomic
+    // teams pack their integration too, the others their pair tests and
+    // goal terms only
     if (P.n <= 2) D4_CASE(2, false);
     else if (P.n <= 4) D4_CASE(4, false);
     else if (P.n <= 8) {
-        if constexpr (kPack) {
-            if (pack) D4_CASE(8, true);
-            else D4_CASE(8, false);
-        } else D4_CASE(8, false);
+        if (I.paired) D4_CASE(8, true);
+        else D4_CASE(8, false);
     } else if (P.n <= 16) {
-        if constexpr (kPack) {
-            if (pack) D4_CASE(16, true);
-            else D4_CASE(16, false);
-        } else D4_CASE(16, false);
+        if (I.paired) D4_CASE(16, true);
+        else D4_CASE(16, false);
     } else D4_CASE(32, false);
 #undef D4_CASE
 }

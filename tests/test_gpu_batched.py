@@ -87,9 +87,10 @@ def test_batched_matches_single_solves(torch, g, oracle_lib, autotune):
 
 @pytest.mark.parametrize("obstacles", [False, True])
 def test_batched_packing_matches_single_solves(torch, g, oracle_lib, obstacles):
-    """Two robots per lane in the batched kernel (2D/3D holonomic teams of
-    5..16 robots, both lane segments, plus a unicycle team and a 3-robot
-    team that keep one robot per lane); the packing flags follow the rule.
+    """Two robots per lane in the batched kernel (teams of 5..16 robots:
+    2D/3D holonomic, unicycle and 4-state differential drive, both lane
+    segments, plus a 3-robot team that keeps one robot per lane); the
+    packing flags follow the rule.
     One denoising step from the same random deformation (warm start at step
     1) evaluates every sample on the same mean controls, so the batched
     solve with one robot per lane, with two, and the single-problem solve
@@ -103,7 +104,7 @@ def test_batched_packing_matches_single_solves(torch, g, oracle_lib, obstacles):
     rng = np.random.default_rng(21)
     cases = [(scenarios.HOLO2D, 5), (scenarios.HOLO2D, 8), (scenarios.HOLO2D, 11), (scenarios.HOLO2D, 16),
              (scenarios.HOLO3D, 6), (scenarios.HOLO3D, 9), (scenarios.HOLO3D, 16), (scenarios.UNICYCLE, 12),
-             (scenarios.HOLO2D, 3)]
+             (scenarios.HOLO2D, 3), (scenarios.UNICYCLE, 6), (scenarios.DIFFDRIVE4, 7)]
     insts = [round_instance(scenarios.box_instance(rng, dyn, n, 30 + 7 * b, 256, K=5))
              for b, (dyn, n) in enumerate(cases)]
     if obstacles:
@@ -113,7 +114,7 @@ def test_batched_packing_matches_single_solves(torch, g, oracle_lib, obstacles):
     du0 = [torch.tensor(scenarios.random_deformation(rng, i), dtype=torch.float32, device="cuda") for i in insts]
     one, full = g.Budget(max_iters=1, start_step=1), g.Budget(max_iters=2)
     batch = g.d4orm_batch_create([p.handle for p in probs], params, autotune=False)
-    want = [1 if dyn in (scenarios.HOLO2D, scenarios.HOLO3D) and 5 <= n <= 16 else 0 for dyn, n in cases]
+    want = [1 if 5 <= n <= 16 else 0 for dyn, n in cases]
     plans = {}
     for mode in (g.PACK_PAIRED, g.PACK_SINGLE):
         g.d4orm_batch_set_packing(batch, mode)
@@ -163,7 +164,7 @@ def test_batched_packing_autotune_rule(torch, g):
     batch = g.d4orm_batch_create([p.handle for p in probs], params, autotune=True)
     pk = g.d4orm_batch_packing(batch, len(insts))
     for b, inst in enumerate(insts):
-        if inst.dyn in (scenarios.HOLO2D, scenarios.HOLO3D) and 5 <= inst.n <= 16:
+        if 5 <= inst.n <= 16:
             single, paired = pk["bucket_ns"][(inst.dyn, "5-8" if inst.n <= 8 else "9-16")]
             assert single > 0 and paired > 0
             assert pk["paired"][b] == (1 if paired < single else 0)
