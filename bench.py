@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--workload", default="holo3d_n16",
                     choices=sorted(scenarios.WORKLOADS) + ["mixed512", "warmstart", "mppi_compare", "sensitivity"])
     ap.add_argument("--teams", type=int, default=200, help="held-out teams for --workload warmstart")
+    ap.add_argument("--batch-count", type=int, default=512,
+                    help="--workload mixed512: problems in the batch (fewer: a smaller case for profiling)")
+    ap.add_argument("--batch-steps", type=int, default=100, help="--workload mixed512: denoising steps K")
+    ap.add_argument("--batch-iters", type=int, default=5, help="--workload mixed512: iteration budget")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -350,10 +354,14 @@ def run_batched(args, torch, g, world, rank):
     holonomic / 3D holonomic / unicycle, 10 m box), N = 1024, 100 steps x up
     to 5 iterations with stop-on-success, in one persistent graph launch.
     The step's sample-rollout count is summed from each problem's iterations."""
-    insts = [f32_inst(i) for i in scenarios.mixed_batch(count=512, seed=2, N=1024)]
+    count, K, iters = args.batch_count, args.batch_steps, args.batch_iters
+    insts = [f32_inst(i) for i in scenarios.mixed_batch(count=count, seed=2, N=1024)]
+    for i in insts:
+        i.K = K
     probs = [g.Problem(i) for i in insts]
-    params = g.Params(n_samples=1024, n_steps=100, seed=0, instance_tag=rank * 512)
-    budget = g.Budget(max_iters=5, stop_on_success=True)
+    params = g.Params(n_samples=1024, n_steps=K, seed=0, instance_tag=rank * count)
+    budget = g.Budget(max_iters=iters, stop_on_success=True)
+    workload = "mixed512_batched" if (count, K, iters) == (512, 100, 5) else f"mixed{count}_K{K}_it{iters}_batched"
     outs = [torch.zeros((i.T, i.n, i.dims[1]), device="cuda") for i in insts]
     batch = g.d4orm_batch_create([p.handle for p in probs], params, autotune=True)
     info = g.d4orm_batch_info(batch)
@@ -412,14 +420,14 @@ def run_batched(args, torch, g, world, rank):
         secs = sum(p_["samples"] / p_["value"] for p_ in parts)
         cpu = {"value": sum(p_["samples"] for p_ in parts) / secs, "unit": UNIT, "cores": parts[0]["cores"],
                "kind": "oracle",
-               "sample": f"{len(picks)} of the 512 problems (every 64th), one denoising step over their first "
+               "sample": f"{len(picks)} of the {count} problems (every 64th), one denoising step over their first "
                          f"samples each, FP64, {parts[0]['cores']} thread(s), {secs:.1f} s"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "mixed512_batched", "problems": len(insts), "samples_N": 1024, "denoise_steps": 100,
-                   "max_iterations": 5, "stop_on_success": True, "sample_rollouts_per_step": per_step,
+        "config": {"workload": workload, "problems": len(insts), "samples_N": 1024, "denoise_steps": K,
+                   "max_iterations": iters, "stop_on_success": True, "sample_rollouts_per_step": per_step,
                    "threads_per_cta": info["threads_per_cta"], "ctas": info["ctas"],
                    "autotune_ms_128_256_512": info["tuned_ms"], "autotune_table": g.d4orm_batch_tuning(batch),
                    "packing": packing_summary(g, batch, len(insts)),
@@ -434,6 +442,10 @@ def run_batched(args, torch, g, world, rank):
                      "traffic": None, "kernel": "k_batched_solve",
                      "peak_basis": "FP32 lanes x 2 x 2070 MHz (152 SMs x 128)", "launch_ms": ms},
         "solved": solved,
+        # share of the CTAs' time spent inside a problem (device clock of
+        # each problem's own solve, summed, over CTAs x the launch): the rest
+        # is the tail after the queue ran dry
+        "cta_busy_fraction": sum(r["ms_total"] for r in results) / (info["ctas"] * ms),
         "median_ms_to_success": statistics.median([r["ms_to_success"] for r in results if r["ms_to_success"] > 0])
         if solved else None,
     }
