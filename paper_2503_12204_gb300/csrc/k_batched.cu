@@ -7,7 +7,7 @@ namespace d4orm {
 
 size_t batched_smem_bytes(const BatchConsts& C)
 {
-    return ((size_t)C.ctrl_cap + C.n_cap + 2ull * C.n_cap) * sizeof(float) + 32ull * 32 * sizeof(float4);
+    return ((size_t)C.ctrl_cap + C.n_cap + 2ull * C.n_cap) * sizeof(float);
 }
 
 cudaError_t prepare_batched(bool obstacles)

@@ -13,8 +13,8 @@
 // Per step the CTA stages the mean controls in shared memory, evaluates all
 // N samples with the same lane-segment code as the single-problem kernel,
 // runs the block softmax with weight compaction, and forms the weighted
-// noise sum quad block by quad block (noise regenerated from the same
-// Philox counters), each quad's per-warp partials added in a fixed order.
+// noise sum with one warp per noise quad (noise regenerated from the same
+// Philox counters), the lanes' partial sums added by a fixed shuffle tree.
 //
 // The kernel is a template on OBS (obstacle penalty compiled in or not);
 // k_batched.cu instantiates the obstacle-free variant and k_batched_obs.cu
@@ -34,7 +34,7 @@ namespace d4orm {
 template <int DYN, int SEG, bool OBS, bool PAIRED>
 __device__ __noinline__ void batched_instance(const DevProblem& P, const BatchInstance& I, const BatchConsts& C,
                                                  const float4* __restrict__ sched, int b, float* sM, float* sFit,
-                                                 float2* sList, float4* sRed, float* sh, int* scan, int* s_count,
+                                                 float2* sList, float* sh, int* scan, int* s_count,
                                                  d4orm_verdict* s_verdict, BatchResult* results, long long t_launch,
                                                  int* s_stop)
 {
@@ -109,17 +109,19 @@ __device__ __noinline__ void batched_instance(const DevProblem& P, const BatchIn
             else
                 softmax_block<0>(sFit, N, S.inv_lambda, sList, s_count, nullptr, sh, scan);
             __syncthreads();
-            // weighted noise sum and Eq. (13) update, 32 quads at a time
+            // weighted noise sum and Eq. (13) update: each warp owns whole
+            // noise quads (quads dealt round-robin over the warps), its lanes
+            // deal the listed samples round-robin, and a fixed shuffle tree
+            // adds the lanes' partial sums -- no CTA barrier until the next
+            // step reads the new deformation
             const int n_list = *s_count;
             const int nQ = P.n * P.Q;
             const int len = P.T * DU;
-            for (int qb = 0; qb < nQ; qb += 32) {
-                const int gq = qb + lane;
-                const bool valid = gq < nQ;
-                const int k = valid ? gq / P.Q : 0;
-                const int q = valid ? gq - k * P.Q : 0;
+            for (int gq = warp; gq < nQ; gq += nw) {
+                const int k = gq / P.Q;
+                const int q = gq - k * P.Q;
                 float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-                for (int e = warp; e < n_list; e += nw) {
+                for (int e = lane; e < n_list; e += 32) {
                     const float2 wj = sList[e];
                     float z[4];
                     noise_quad(S, c3, (uint32_t)q, (uint32_t)__float_as_int(wj.y), (uint32_t)k, z);
@@ -128,27 +130,25 @@ __device__ __noinline__ void batched_instance(const DevProblem& P, const BatchIn
                     a.z = fmaf(wj.x, z[2], a.z);
                     a.w = fmaf(wj.x, z[3], a.w);
                 }
-                sRed[warp * 32 + lane] = a;
-                __syncthreads();
-                if (warp == 0 && valid) {
-                    float4 s = sRed[lane];
-                    for (int r = 1; r < nw; ++r) {
-                        const float4 o = sRed[r * 32 + lane];
-                        s.x += o.x; s.y += o.y; s.z += o.z; s.w += o.w;
-                    }
-                    const float sv[4] = {s.x, s.y, s.z, s.w};
 #pragma unroll
-                    for (int r4 = 0; r4 < 4; ++r4) {
-                        const int e = 4 * q + r4;
-                        if (e < len) {
-                            const int t = e / DU, d = e - t * DU;
-                            const int idx = (t * P.n + k) * DU + d;
-                            du[cur ^ 1][idx] = S.g * fmaf(S.sigma, sv[r4], S.c * du[cur][idx]);
-                        }
+                for (int off = 16; off >= 1; off >>= 1) {
+                    a.x += __shfl_xor_sync(kFull, a.x, off);
+                    a.y += __shfl_xor_sync(kFull, a.y, off);
+                    a.z += __shfl_xor_sync(kFull, a.z, off);
+                    a.w += __shfl_xor_sync(kFull, a.w, off);
+                }
+                // lane r4 < 4 writes element 4q + r4
+                if (lane < 4) {
+                    const float sv = lane == 0 ? a.x : lane == 1 ? a.y : lane == 2 ? a.z : a.w;
+                    const int e = 4 * q + lane;
+                    if (e < len) {
+                        const int t = e / DU, d = e - t * DU;
+                        const int idx = (t * P.n + k) * DU + d;
+                        du[cur ^ 1][idx] = S.g * fmaf(S.sigma, sv, S.c * du[cur][idx]);
                     }
                 }
-                __syncthreads();
             }
+            __syncthreads();
             cur ^= 1;
         }
         if (stop) break;  // an interrupted iteration is discarded: tau.u keeps the completed ones
@@ -180,11 +180,11 @@ __device__ __noinline__ void batched_instance(const DevProblem& P, const BatchIn
 template <int DYN, bool OBS>
 __device__ __forceinline__ void batched_dispatch_seg(const DevProblem& P, const BatchInstance& I,
                                                      const BatchConsts& C, const float4* sched, int b, float* sM,
-                                                     float* sFit, float2* sList, float4* sRed, float* sh, int* scan,
+                                                     float* sFit, float2* sList, float* sh, int* scan,
                                                      int* s_count, d4orm_verdict* s_verdict, BatchResult* results,
                                                      long long t_launch, int* s_stop)
 {
-#define D4_CASE(SEGV, PV) batched_instance<DYN, SEGV, OBS, PV>(P, I, C, sched, b, sM, sFit, sList, sRed, sh, scan, \
+#define D4_CASE(SEGV, PV) batched_instance<DYN, SEGV, OBS, PV>(P, I, C, sched, b, sM, sFit, sList, sh, scan, \
                                                            s_count, s_verdict, results, t_launch, s_stop)
     // robot-lane packing (I.paired, chosen per problem by the autotuner) is
     // compiled for the 8- and 16-lane segments (5..16 robots); holonomic
@@ -218,7 +218,6 @@ k_batched_solve(const DevProblem* __restrict__ probs, const BatchInstance* __res
     float* sM = reinterpret_cast<float*>(dyn_smem);                 // [C.ctrl_cap]
     float* sFit = sM + C.ctrl_cap;                                  // [C.n_cap]
     float2* sList = reinterpret_cast<float2*>(sFit + C.n_cap);      // [C.n_cap]
-    float4* sRed = reinterpret_cast<float4*>(sList + C.n_cap);      // [32 warps][32]
     if (threadIdx.x == 0) s_launch = globaltimer_ns();  // every CTA is resident from the launch on
     __syncthreads();
     const long long t_launch = s_launch;
@@ -235,19 +234,19 @@ k_batched_solve(const DevProblem* __restrict__ probs, const BatchInstance* __res
         const BatchInstance I = insts[b];
         switch (sP.dyn) {
         case HOLO2D:
-            batched_dispatch_seg<HOLO2D, OBS>(sP, I, C, sched, b, sM, sFit, sList, sRed, sh, scan, &s_count, &s_verdict,
+            batched_dispatch_seg<HOLO2D, OBS>(sP, I, C, sched, b, sM, sFit, sList, sh, scan, &s_count, &s_verdict,
                                          results, t_launch, &s_stop);
             break;
         case HOLO3D:
-            batched_dispatch_seg<HOLO3D, OBS>(sP, I, C, sched, b, sM, sFit, sList, sRed, sh, scan, &s_count, &s_verdict,
+            batched_dispatch_seg<HOLO3D, OBS>(sP, I, C, sched, b, sM, sFit, sList, sh, scan, &s_count, &s_verdict,
                                          results, t_launch, &s_stop);
             break;
         case UNICYCLE:
-            batched_dispatch_seg<UNICYCLE, OBS>(sP, I, C, sched, b, sM, sFit, sList, sRed, sh, scan, &s_count,
+            batched_dispatch_seg<UNICYCLE, OBS>(sP, I, C, sched, b, sM, sFit, sList, sh, scan, &s_count,
                                            &s_verdict, results, t_launch, &s_stop);
             break;
         default:
-            batched_dispatch_seg<DIFFDRIVE4, OBS>(sP, I, C, sched, b, sM, sFit, sList, sRed, sh, scan, &s_count,
+            batched_dispatch_seg<DIFFDRIVE4, OBS>(sP, I, C, sched, b, sM, sFit, sList, sh, scan, &s_count,
                                              &s_verdict, results, t_launch, &s_stop);
             break;
         }
