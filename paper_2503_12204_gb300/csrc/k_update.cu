@@ -63,17 +63,27 @@ k_weighted_mean(const DevProblem P, const DevStep S, const float2* __restrict__ 
     const uint32_t c3 = iter_word(S, it_dev);
     const int n_list = *count;
     float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+    // two entries per trip: their Philox chains are independent, so one
+    // thread keeps two in flight; they are added in list order
     int e = slice;
-    float2 next = e < n_list ? list[e] : make_float2(0.0f, 0.0f);
-    for (; e < n_list; e += SL) {
-        const float2 wj = next;
-        if (e + SL < n_list) next = list[e + SL];
+    for (; e + SL < n_list; e += 2 * SL) {
+        const float2 w0 = list[e], w1 = list[e + SL];
+        float z[4], y[4];
+        noise_quad(S, c3, (uint32_t)q, (uint32_t)__float_as_int(w0.y), (uint32_t)k, z);
+        noise_quad(S, c3, (uint32_t)q, (uint32_t)__float_as_int(w1.y), (uint32_t)k, y);
+        a0 = fmaf(w1.x, y[0], fmaf(w0.x, z[0], a0));
+        a1 = fmaf(w1.x, y[1], fmaf(w0.x, z[1], a1));
+        a2 = fmaf(w1.x, y[2], fmaf(w0.x, z[2], a2));
+        a3 = fmaf(w1.x, y[3], fmaf(w0.x, z[3], a3));
+    }
+    if (e < n_list) {
+        const float2 w0 = list[e];
         float z[4];
-        noise_quad(S, c3, (uint32_t)q, (uint32_t)__float_as_int(wj.y), (uint32_t)k, z);
-        a0 = fmaf(wj.x, z[0], a0);
-        a1 = fmaf(wj.x, z[1], a1);
-        a2 = fmaf(wj.x, z[2], a2);
-        a3 = fmaf(wj.x, z[3], a3);
+        noise_quad(S, c3, (uint32_t)q, (uint32_t)__float_as_int(w0.y), (uint32_t)k, z);
+        a0 = fmaf(w0.x, z[0], a0);
+        a1 = fmaf(w0.x, z[1], a1);
+        a2 = fmaf(w0.x, z[2], a2);
+        a3 = fmaf(w0.x, z[3], a3);
     }
     // lanes lane and lane ^ off (off >= QC) hold the same quad
 #pragma unroll
