@@ -42,33 +42,6 @@ __device__ float block_reduce(float v, float* sh)
     return r;
 }
 
-// Block-wide sum and maximum in one round (sh: at least 66 floats).
-__device__ __forceinline__ void block_reduce_sum_max(float& s, float& m, float* sh)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    s = warp_sum(s);
-    m = warp_max(m);
-    if (lane == 0) {
-        sh[warp] = s;
-        sh[33 + warp] = m;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        float a = lane < nw ? sh[lane] : 0.0f;
-        float b = lane < nw ? sh[33 + lane] : -INFINITY;
-        a = warp_sum(a);
-        b = warp_max(b);
-        if (lane == 0) {
-            sh[32] = a;
-            sh[65] = b;
-        }
-    }
-    __syncthreads();
-    s = sh[32];
-    m = sh[65];
-    __syncthreads();
-}
-
 // Samples whose unnormalised weight exp(l_j - max l) falls below 2^-30
 // are left out of the weighted sum: together they move it by at most
 // N * 2^-30 * max|eps| relative to the largest weight (max|eps| <= 5.77 for
@@ -82,15 +55,27 @@ constexpr float kLogWeightCut = -20.794415f;  // -30 ln 2
 // Batch normalisation (Sec. IV-C) + temperature softmax (Eq. (6)) of the N
 // rewards in `fitness` (global or shared memory), by the whole thread block:
 // writes the ordered (weight, index) list of the samples that carry weight
-// and its length.  sh[66], scan[33]: shared scratch.  VR > 0 keeps each
-// thread's (at most VR) values in registers.
+// and its length.  sh[kSoftmaxScratch], scan[33]: shared scratch.  VR > 0
+// keeps each thread's (at most VR) values in registers.
+//
+// Two block-wide rounds, two barriers each:
+//  1. sum and sum of squares of r - r_0 (shifted by the first reward, so the
+//     population variance E[(r - r_0)^2] - E[r - r_0]^2 loses no precision
+//     to a large common offset) and the largest reward -- the largest logit
+//     is that reward's, (r - mu) * scale being monotone in r;
+//  2. the sum of exp(l - max l) and an exclusive scan of the per-thread
+//     counts of weights at or above the cut, which places each thread's
+//     survivors in the list.
 // ---------------------------------------------------------------------------
+constexpr int kSoftmaxScratch = 100;
+
 template <int VR>
-__device__ __forceinline__ void softmax_block(const float* __restrict__ fitness, int N, float inv_lambda,
+__device__ __noinline__ void softmax_block(const float* __restrict__ fitness, int N, float inv_lambda,
                                               float2* __restrict__ list, int* __restrict__ count,
                                               float* __restrict__ stats, float* sh, int* scan)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     // contiguous ranges keep the compacted list in sample order
     const int per = (N + nt - 1) / nt;
     const int j0 = min(N, tid * per), j1 = min(N, j0 + per);
@@ -111,24 +96,47 @@ __device__ __forceinline__ void softmax_block(const float* __restrict__ fitness,
             for (int i = 0; i < cnt; ++i) f(i, fitness[j0 + i]);
         }
     };
-    // sum and largest reward in one reduction: the largest logit is the
-    // logit of the largest reward, (x - mu) * scale being monotone in x
-    float s = 0.0f, mx = -INFINITY;
+    // round 1: shifted sum, shifted sum of squares, maximum
+    const float r0 = fitness[0];
+    float s1 = 0.0f, s2 = 0.0f, mx = -INFINITY;
     each([&](int, float x) {
-        s += x;
+        const float d = x - r0;
+        s1 += d;
+        s2 = fmaf(d, d, s2);
         mx = fmaxf(mx, x);
     });
-    block_reduce_sum_max(s, mx, sh);
-    const float mu = s / (float)N;
-    float v = 0.0f;
-    each([&](int, float x) {
-        const float d = x - mu;
-        v = fmaf(d, d, v);
-    });
-    const float sd = sqrtf(block_reduce<false>(v, sh) / (float)N);
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    mx = warp_max(mx);
+    if (lane == 0) {
+        sh[warp] = s1;
+        sh[32 + warp] = s2;
+        sh[64 + warp] = mx;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        float a = lane < nw ? sh[lane] : 0.0f;
+        float b = lane < nw ? sh[32 + lane] : 0.0f;
+        float c = lane < nw ? sh[64 + lane] : -INFINITY;
+        a = warp_sum(a);
+        b = warp_sum(b);
+        c = warp_max(c);
+        if (lane == 0) {
+            sh[96] = a;
+            sh[97] = b;
+            sh[98] = c;
+        }
+    }
+    __syncthreads();
+    const float inv_n = 1.0f / (float)N;
+    const float dm = sh[96] * inv_n;
+    const float mu = r0 + dm;
+    const float sd = sqrtf(fmaxf(fmaf(-dm, dm, sh[97] * inv_n), 0.0f));
+    mx = sh[98];
     const bool degenerate = !(sd > 1e-12f * fmaxf(1.0f, fabsf(mu)));
     const float scale = degenerate ? 0.0f : inv_lambda / sd;
     const float m = (mx - mu) * scale;
+    // round 2: sum of exp(l - m) and the survivors' exclusive scan
     float z = 0.0f;
     int kept = 0;
     each([&](int, float x) {
@@ -136,30 +144,33 @@ __device__ __forceinline__ void softmax_block(const float* __restrict__ fitness,
         z += expf(l);
         kept += l >= kLogWeightCut ? 1 : 0;
     });
-    const float Z = block_reduce<false>(z, sh);
-    const float invZ = 1.0f / Z;
-    // exclusive scan of the per-thread survivor counts
-    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    z = warp_sum(z);
     int incl = kept;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
         const int o = __shfl_up_sync(kFull, incl, off);
         if (lane >= off) incl += o;
     }
+    // the scratch of round 1 is free: every thread has read its results
     if (lane == 31) scan[warp] = incl;
+    if (lane == 0) sh[warp] = z;
     __syncthreads();
     if (warp == 0) {
-        int t = lane < nw ? scan[lane] : 0;
+        const int t = lane < nw ? scan[lane] : 0;
         int ti = t;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const int o = __shfl_up_sync(kFull, ti, off);
             if (lane >= off) ti += o;
         }
+        const float zz = warp_sum(lane < nw ? sh[lane] : 0.0f);
         if (lane < nw) scan[lane] = ti - t;
         if (lane == 31) scan[32] = ti;
+        if (lane == 0) sh[99] = zz;
     }
     __syncthreads();
+    const float Z = sh[99];
+    const float invZ = 1.0f / Z;
     int pos = scan[warp] + incl - kept;
     each([&](int i, float x) {
         const float l = (x - mu) * scale - m;

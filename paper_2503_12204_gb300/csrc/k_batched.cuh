@@ -209,7 +209,7 @@ k_batched_solve(const DevProblem* __restrict__ probs, const BatchInstance* __res
                 BatchResult* results)
 {
     __shared__ DevProblem sP;
-    __shared__ float sh[66];
+    __shared__ float sh[kSoftmaxScratch];
     __shared__ int scan[33];
     __shared__ int s_pick, s_count, s_stop;
     __shared__ d4orm_verdict s_verdict;

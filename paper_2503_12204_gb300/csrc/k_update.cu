@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(kSoftmaxThreads)
 k_softmax_weights(const float* __restrict__ fitness, int N, float inv_lambda, float2* __restrict__ list,
                   int* __restrict__ count, float* __restrict__ stats)
 {
-    __shared__ float sh[66];
+    __shared__ float sh[kSoftmaxScratch];
     __shared__ int scan[33];
     softmax_block<VR>(fitness, N, inv_lambda, list, count, stats, sh, scan);
 }
