@@ -296,6 +296,30 @@ def test_mppi_differs_from_the_schedule(torch, g):
     assert np.array_equal(outs[1], outs[2])
 
 
+@pytest.mark.parametrize("N", [200, 3000, 9000])
+def test_equal_rewards_give_uniform_weights(torch, g, N):
+    """Sec. IV-C normalisation when every sample scores the same: a spread
+    of 1e-30 around a mean of whole controls moves no position in binary32,
+    so all N rewards are bit-equal, the population std is 0 and the weights
+    fall back to uniform (no division by zero, no NaN): the MPPI update then
+    returns the deformation it was given to within 1e-30 * max|eps|.  N
+    spans one and several rewards per softmax thread and the re-reading
+    path above 8192."""
+    inst = small_instance(0, 4, 20, N, seed=2, K=50)
+    rng = np.random.default_rng(9)
+    ub = dev(torch, np.round(scenarios.random_controls(rng, inst, 0.5), 1))
+    du = torch.zeros_like(ub)
+    prob = g.Problem(inst)
+    p = gpu_params(g, inst, update=(1, 1e-30))
+    o, f = torch.full_like(du, float("nan")), torch.zeros(N, device="cuda")
+    g.d4orm_denoise_step(prob.handle, p, 0, 20, ub, du, o, f)
+    torch.cuda.synchronize()
+    fit = host(f)
+    assert np.all(fit == fit[0])
+    out = host(o)
+    assert np.all(np.isfinite(out)) and np.abs(out).max() <= 1e-28
+
+
 def test_mppi_solve_verdict_parity(torch, g, oracle_lib):
     """A 2-robot swap solved with the MPPI rule by both implementations: the
     oracle re-judges the GPU's plan with the GPU's verdict, and both reach
