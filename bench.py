@@ -92,6 +92,7 @@ def flops_per_sample_rollout(inst) -> int:
 # (summaries and commands in profiles/); a kernel changed since its capture
 # must be dropped from this table (its traffic is then reported as null).
 NCU_TRAFFIC_BYTES = {
+    ("k_rollout_fitness_paired", "holo3d_n16_T100_N8192"): 86016,
     ("k_rollout_fitness_pipe", "unicycle_n8_T100_N2048"): 38400,
     ("k_rollout_fitness", "unicycle_n8_T100_N2048"): 45824,
 }
