@@ -329,7 +329,8 @@ typedef struct d4orm_batch d4orm_batch;
  * per lane wherever the kernel has that rollout.
  * Errors: INVALID_ARG (null arguments, bad params, tags beyond
  * D4ORM_MAX_TAG), UNSUPPORTED (n_samples > D4ORM_BATCH_MAX_SAMPLES, or
- * shared memory for the largest problem above 200 KB), OOM, CUDA. */
+ * shared memory above 200 KB: 4 bytes per control of the largest problem,
+ * 12 per sample, and 24 KB of per-warp position buffers), OOM, CUDA. */
 d4orm_status d4orm_batch_create(d4orm_problem *const *problems, int count, const d4orm_params *params,
                                 int autotune, d4orm_batch **out);
 

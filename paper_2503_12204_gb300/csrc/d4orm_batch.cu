@@ -178,10 +178,10 @@ d4orm_status d4orm_batch_create(d4orm_problem* const* problems, int count, const
     B->C.w_safe = params->w_safe;
     B->C.inv_lambda = S1.inv_lambda;
     B->smem = batched_smem_bytes(B->C);
-    if (B->smem > 200 * 1024) {
+    if (B->smem + batched_xbuf_bytes(kBatchMaxThreads) > 200 * 1024) {
         delete B;
         return set_error(D4ORM_ERR_UNSUPPORTED, "batched solve: largest problem and N need more than 200 KB of "
-                                                "shared memory");
+                                                "shared memory (with the 24 KB of position buffers)");
     }
 
     auto fail_cleanup = [&](d4orm_status st) {

@@ -96,6 +96,9 @@ struct BatchResult {
 // `obstacles` selects the kernel variant with the obstacle penalty compiled
 // in (any problem of the batch has obstacles).
 size_t batched_smem_bytes(const BatchConsts& C);
+// Shared memory of the paired rollouts' per-warp position buffers at
+// `threads` per CTA (on top of batched_smem_bytes).
+size_t batched_xbuf_bytes(int threads);
 cudaError_t prepare_batched(bool obstacles);
 int batched_ctas_per_sm(bool obstacles, int threads, size_t smem);
 cudaError_t launch_batched(bool obstacles, const DevProblem* probs, const BatchInstance* insts, const int* order,

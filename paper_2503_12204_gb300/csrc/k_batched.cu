@@ -10,6 +10,8 @@ size_t batched_smem_bytes(const BatchConsts& C)
     return ((size_t)C.ctrl_cap + C.n_cap + 2ull * C.n_cap) * sizeof(float);
 }
 
+size_t batched_xbuf_bytes(int threads) { return (size_t)(threads / 32) * kXbufPerWarp * sizeof(f2); }
+
 cudaError_t prepare_batched(bool obstacles)
 {
     return obstacles ? prepare_batched_obs() : BatchedOps<false>::prepare();

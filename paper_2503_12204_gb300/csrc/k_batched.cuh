@@ -29,8 +29,18 @@
 
 namespace d4orm {
 
+// Per-warp buffers of the paired rollouts' position exchange, after the
+// weight list in dynamic shared memory: 2 step parities x 3 coordinates x
+// 32 lanes of packed pairs.
+constexpr int kXbufPerWarp = 2 * 3 * 32;  // f2 entries
+__device__ __forceinline__ f2* batched_xbuf(float2* sList, const BatchConsts& C)
+{
+    return reinterpret_cast<f2*>(sList + C.n_cap);
+}
+
 // PAIRED: the samples' rollouts use two robots per lane (L = SEG/2 lanes
-// per sample, f32x2 arithmetic), otherwise one robot per lane.
+// per sample, f32x2 arithmetic, partners' positions through the warp's
+// shared-memory buffer), otherwise one robot per lane.
 template <int DYN, int SEG, bool OBS, bool PAIRED>
 __device__ __noinline__ void batched_instance(const DevProblem& P, const BatchInstance& I, const BatchConsts& C,
                                                  const float4* __restrict__ sched, int b, float* sM, float* sFit,
@@ -98,7 +108,9 @@ __device__ __noinline__ void batched_instance(const DevProblem& P, const BatchIn
             for (int base = 0; base < N; base += nw * SPW) {
                 const int j = base + warp * SPW + lane / LPS;
                 float f;
-                if constexpr (PAIRED) f = sample_fitness_paired<DYN, LPS, OBS>(P, S, sM, c3, j);
+                if constexpr (PAIRED)
+                    f = sample_fitness_paired<DYN, LPS, OBS, true>(P, S, sM, c3, j,
+                                                                   batched_xbuf(sList, C) + warp * kXbufPerWarp);
                 else f = sample_fitness_segment<DYN, SEG, OBS>(P, S, sM, c3, j);
                 if ((lane & (LPS - 1)) == 0 && j < N) sFit[j] = f;
             }
@@ -264,7 +276,8 @@ struct BatchedOps {
     static int ctas_per_sm(int threads, size_t smem)
     {
         int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched_solve<OBS>, threads, smem) != cudaSuccess) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched_solve<OBS>, threads,
+                                                          smem + batched_xbuf_bytes(threads)) != cudaSuccess) {
             cudaGetLastError();
             return 0;
         }
@@ -274,7 +287,8 @@ struct BatchedOps {
                               const float4* sched, const BatchConsts& C, int* queue, BatchResult* results, int grid,
                               int threads, cudaStream_t st)
     {
-        k_batched_solve<OBS><<<grid, threads, batched_smem_bytes(C), st>>>(probs, insts, order, sched, C, queue,
+        k_batched_solve<OBS><<<grid, threads, batched_smem_bytes(C) + batched_xbuf_bytes(threads), st>>>(
+            probs, insts, order, sched, C, queue,
                                                                            results);
         return cudaGetLastError();
     }
