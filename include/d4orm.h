@@ -179,11 +179,12 @@ void d4orm_problem_destroy(d4orm_problem *problem);
  * arithmetic issues as packed f32x2 instructions.  PIPELINE: one rollout
  * warp per 32/SEG samples plus helper warps that generate the noise of the
  * next time chunk and score the previous one (for batches too small to
- * fill the GPU with the register kernel).  AUTO picks PIPELINE when the
- * register kernel would have fewer than 2.5 warps per SM, PAIRED when the
- * paired kernel still has at least 3 warps per scheduler (12 per SM) and
- * n >= 2, else REGISTER (the pipelined kernel also needs its shared memory
- * to fit in 200 KB).  All compute the same fitness (summation order
+ * fill the GPU with the register kernel).  AUTO picks PAIRED for 2D/3D
+ * holonomic teams of n >= 5 when the paired kernel has at least 6 warps per
+ * SM (12 with obstacles), else PIPELINE when the register kernel would have
+ * fewer than 2.5 warps per SM, else REGISTER (the pipelined kernel also
+ * needs its shared memory to fit in 200 KB); the thresholds are measured
+ * crossovers on GB300.  All compute the same fitness (summation order
  * aside). */
 typedef enum {
     D4ORM_ROLLOUT_AUTO = 0,

@@ -153,12 +153,18 @@ int resolve_rollout_kernel(const DevProblem& P, int N, int sm_count, int request
     if (requested == D4ORM_ROLLOUT_REGISTER) return D4ORM_ROLLOUT_REGISTER;
     const int seg = P.n <= 1 ? 1 : P.n <= 2 ? 2 : P.n <= 4 ? 4 : P.n <= 8 ? 8 : P.n <= 16 ? 16 : 32;
     const long long warps = ((long long)N * seg + 31) / 32;
-    // automatic: with at least 3 warps per scheduler left after halving the
-    // warps, two robots per lane win (measured on GB300, 16 3D robots,
-    // N = 8192: 2048 paired warps 94.6 us vs 4096 register warps 100.5 us;
-    // the packed arithmetic needs fewer issue slots per robot-step)
+    // automatic: two robots per lane for holonomic teams of 5 or more robots
+    // once the paired kernel keeps 6 warps per SM busy (12 with obstacles,
+    // whose test does not pack).  Measured on GB300 inside CUDA graphs, us,
+    // register vs paired: 3D n = 16, N = 2048 / 3072 / 4096 / 8192 ->
+    // 33.2/34.4, 45.0/48.6, 55.1/48.9, 93.0/86.6; 2D n = 16, N = 4096:
+    // 40.6/36.0; 3D n = 8, N = 4096 / 8192: 27.1/28.1, 46.0/38.9; 2D n = 16
+    // with 4 obstacles, N = 4096 / 8192: 56.7/67.6, 96.4/96.5; unicycle
+    // n = 8, N = 2048 / 8192: 15.1/33.5, 37.6/42.3 (never paired).
     const long long paired_warps = ((long long)N * paired_lanes(P.n) + 31) / 32;
-    if (P.n >= 2 && paired_warps >= 12LL * sm_count) return D4ORM_ROLLOUT_PAIRED;
+    const bool holonomic = P.dyn == HOLO2D || P.dyn == HOLO3D;
+    const long long paired_need = (P.n_obs > 0 ? 12LL : 6LL) * sm_count;
+    if (holonomic && P.n >= 5 && paired_warps >= paired_need) return D4ORM_ROLLOUT_PAIRED;
     if (!pipe_fits) return D4ORM_ROLLOUT_REGISTER;
     // below about 2.5 warps per SM the register kernel leaves the SMs too
     // idle and the pipelined kernel's parallelism along time wins (measured

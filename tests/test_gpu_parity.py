@@ -456,15 +456,20 @@ def test_denoise_step_at_the_control_size_limit(torch, g, oracle_lib):
 
 
 def test_auto_rollout_kernel_choice(torch, g):
-    """AUTO: two robots per lane for the 16-robot 3D workload (2048 paired
-    warps, above 3 per scheduler), one robot per lane for the 8-robot
-    unicycle workload, the pipelined kernel for the 4-robot workload."""
-    expect = {"holo3d_n16": g.ROLLOUT_PAIRED, "unicycle_n8": g.ROLLOUT_REGISTER, "holo2d_n4": g.ROLLOUT_PIPELINE}
-    for name, kind in expect.items():
+    """AUTO on the 152-SM GB300: two robots per lane for holonomic teams of
+    5+ robots from 6 paired warps per SM (12 with obstacles), never for
+    unicycle teams; the pipelined kernel for the small 4-robot workload."""
+    if torch.cuda.get_device_properties(0).multi_processor_count != 152:
+        pytest.skip("thresholds are stated for 152 SMs")
+    expect = [("holo3d_n16", None, g.ROLLOUT_PAIRED), ("holo3d_n16", 4096, g.ROLLOUT_PAIRED),
+              ("holo3d_n16", 3072, g.ROLLOUT_REGISTER), ("obstacles4_n16", None, g.ROLLOUT_REGISTER),
+              ("obstacles4_n16", 8192, g.ROLLOUT_PAIRED), ("unicycle_n8", None, g.ROLLOUT_REGISTER),
+              ("unicycle_n8", 65536, g.ROLLOUT_REGISTER), ("holo2d_n4", None, g.ROLLOUT_PIPELINE),
+              ("holo2d_n4", 65536, g.ROLLOUT_REGISTER)]
+    for name, N, kind in expect:
         inst = round_instance(scenarios.WORKLOADS[name]())
         prob = g.Problem(inst)
-        if torch.cuda.get_device_properties(0).multi_processor_count == 152:
-            assert g.d4orm_problem_rollout_kernel(prob.handle, inst.N) == kind, name
+        assert g.d4orm_problem_rollout_kernel(prob.handle, N or inst.N) == kind, (name, N)
 
 
 @pytest.mark.parametrize("kernel", [1, 2, 3])
