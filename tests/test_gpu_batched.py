@@ -321,3 +321,56 @@ def test_single_solve_cancel(torch, g):
     assert float(u.abs().max()) == 0.0
     r = g.d4orm_solve(prob.handle, p, g.Budget(max_iters=2), u)
     assert r["iters_run"] == 2 and r["stop_reason"] == g.STOP_BUDGET
+
+
+def test_full_size_ragged_batch(torch, g, oracle_lib):
+    """The ragged-batch workload at full size in the benchmark's launch
+    configuration (512 teams, N = 1024, 100 steps x up to 5 iterations,
+    stop on success, autotuned CTA width and packing).  Checked where the
+    oracle can follow: (a) one denoising step of the whole batch from a
+    common random deformation equals, for every 32nd team, the
+    single-problem step with the same tag (1e-4 of the plan's scale: only
+    the order of float sums differs); (b) the full solve's bookkeeping
+    holds for every team; (c) for every 32nd team the oracle's FP64
+    rollout of the GPU's final plan gives the same verdict where the plan
+    is not within 2e-4 m of a threshold, and the same Eq. (3) reward."""
+    insts = [round_instance(i) for i in scenarios.mixed_batch(count=512, seed=2, N=1024)]
+    probs = [g.Problem(i) for i in insts]
+    params = g.Params(n_samples=1024, n_steps=100, seed=0, instance_tag=0)
+    batch = g.d4orm_batch_create([p.handle for p in probs], params, autotune=True)
+    rng = np.random.default_rng(31)
+    du0 = [torch.tensor(scenarios.random_deformation(rng, i), dtype=torch.float32, device="cuda") for i in insts]
+    outs = [torch.zeros((i.T, i.n, i.dims[1]), device="cuda") for i in insts]
+    g.d4orm_batch_solve(batch, g.Budget(max_iters=1, start_step=1), outs, du_init_devs=du0)
+    torch.cuda.synchronize()
+    picks = range(0, 512, 32)
+    for b in picks:
+        single = g.Params(n_samples=1024, n_steps=100, seed=0, instance_tag=b)
+        u = torch.zeros_like(outs[b])
+        g.d4orm_solve(probs[b].handle, single, g.Budget(max_iters=1, start_step=1), u, du_init_dev=du0[b])
+        s, a = u.cpu().numpy(), outs[b].cpu().numpy()
+        scale = max(np.abs(s).max(), 1e-3)
+        assert np.abs(a - s).max() <= 1e-4 * scale, (b, np.abs(a - s).max(), scale)
+    outs = [torch.zeros((i.T, i.n, i.dims[1]), device="cuda") for i in insts]
+    res = g.d4orm_batch_solve(batch, g.Budget(max_iters=5, stop_on_success=True), outs)
+    torch.cuda.synchronize()
+    for r in res:
+        assert 1 <= r["iters_run"] <= 5 and r["stop_reason"] == g.STOP_BUDGET
+        if r["first_success_iter"] >= 0:
+            assert r["iters_run"] == r["first_success_iter"] + 1
+            assert r["verdict"]["collision_free"] and r["verdict"]["goal_reached"]
+        else:
+            assert r["iters_run"] == 5
+    for b in picks:
+        inst = insts[b]
+        op = oracle_problem(oracle_lib, inst)
+        st = oracle_lib.rollout(op, outs[b].cpu().numpy().astype(np.float64))
+        vo = oracle_lib.verdict(op, inst.w_safe, st)
+        v = res[b]["verdict"]
+        if inst.n < 2 or abs(vo["min_pair_dist"] - 2 * inst.radius) > DELTA:
+            assert v["collision_free"] == vo["collision_free"], b
+        fin = np.linalg.norm(st[-1, :, :inst.dims[2]] - inst.goal[:, :inst.dims[2]], axis=1)
+        if np.all(np.abs(fin - inst.goal_tol) > DELTA):
+            assert v["goal_reached"] == vo["goal_reached"], b
+        assert abs(v["reward"] - vo["reward"]) <= 1e-3 * abs(vo["reward"]) + 1e-4 + inst.w_safe / inst.T, b
+    g.d4orm_batch_destroy(batch)
