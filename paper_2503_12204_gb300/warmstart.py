@@ -325,6 +325,13 @@ def evaluate_only(torch, args):
     held = held_out_teams(args.held_out, args.min_robots, args.max_teams)
     res, rows = evaluate(torch, ws, held, Params(n_samples=args.eval_samples, n_steps=100, seed=4, instance_tag=0),
                          args.start_step, args.eval_iters, log=print)
+    if args.held_out_16 > 0:
+        # the target's population: 16-robot held-out teams (seed 5), a longer budget
+        teams16 = scenarios_set(args.held_out_16, seed=5, n_lo=16)
+        res16, _ = evaluate(torch, ws, teams16, Params(n_samples=args.eval_samples, n_steps=100, seed=5,
+                                                       instance_tag=0), args.start_step, args.eval_iters_16, log=print)
+        res["held_out_16"] = dict(teams=args.held_out_16, eval_iters=args.eval_iters_16, all=res16["all"],
+                                  batched=res16["batched"])
     d4orm_warmstart_destroy(ws)
     res.update(teams=len(held), min_robots=args.min_robots, eval_iters=args.eval_iters, weights_meta=meta)
     with open(os.path.join(args.out, "warmstart_eval_only.json"), "w") as f:
