@@ -17,13 +17,12 @@
 // takes its own pair and the robot pairs of lanes a + s (mod L) for
 // s = 1..L/2, and returns the minima it found for the partner's robots to
 // lane a + s with one shuffle (for s = L/2 both lanes of a pair evaluate it).
-// The partners' positions arrive by shuffles, or (XS) from a per-warp
-// shared-memory buffer that every lane writes once per step: one 64-bit
-// load brings both robots of a partner lane already packed, where the
-// shuffles need two per coordinate and a repack.  Both the stand-alone
-// kernel (K2b: 87.2 -> 86.5 us on the 16-robot 3D workload) and the batched
-// solver (167.7 -> 170.2 M sample-rollouts/s on 512 ragged teams) use the
-// buffer.
+// The partners' positions come from a per-warp shared-memory buffer that
+// every lane writes once per step: one 64-bit load brings both robots of a
+// partner lane already packed, where shuffles need two per coordinate and
+// a repack (with shuffles the stand-alone kernel took 87.2 us instead of
+// 86.5 on the 16-robot 3D workload, and the batched solver ran 167.7
+// instead of 170.2 M sample-rollouts/s on 512 ragged teams).
 #pragma once
 
 #include "d4orm_kernels.cuh"
@@ -63,13 +62,12 @@ __device__ __forceinline__ f2 f2_clamp(f2 v, float lo, float hi)
 {
     return f2_pack(clampf(f2_lo(v), lo, hi), clampf(f2_hi(v), lo, hi));
 }
-// XS: the partners' positions are read from a per-warp shared-memory
-// buffer `xbuf` (2 x DP x 32 packed pairs, double-buffered by step parity)
-// instead of by shuffles.
-template <int DYN, int L, bool OBS, bool XS = false>
+// xbuf: this warp's position buffer in shared memory, 2 x DP x 32 packed
+// pairs (double-buffered by step parity), 8-byte aligned.
+template <int DYN, int L, bool OBS>
 __device__ __forceinline__ float sample_fitness_paired(const DevProblem& P, const DevStep& S,
                                                        const float* __restrict__ sM, uint32_t c3, int j,
-                                                       f2* xbuf = nullptr)
+                                                       f2* __restrict__ xbuf)
 {
     using D = DynDims<DYN>;
     constexpr int DX = D::DX, DU = D::DU, DP = D::DP;
@@ -162,62 +160,37 @@ __device__ __forceinline__ float sample_fitness_paired(const DevProblem& P, cons
             m0 = d2;
             m1 = d2;
         }
-        if constexpr (XS) {
-            // own positions to the buffer of this step's parity; the lane's
-            // two robots swapped once, so that (k1, k0) - (p0, p1) gives the
-            // cross pairs of every offset
-            f2* buf = xbuf + (t & 1) * (DP * 32);
-            f2 xs[DP];
+        // own positions to the buffer of this step's parity; the lane's
+        // two robots swapped once, so that (k1, k0) - (p0, p1) gives the
+        // cross pairs of every offset
+        f2* buf = xbuf + (t & 1) * (DP * 32);
+        f2 xs[DP];
+#pragma unroll
+        for (int d = 0; d < DP; ++d) {
+            buf[d * 32 + lane] = x[d];
+            xs[d] = f2_pack(f2_hi(x[d]), f2_lo(x[d]));
+        }
+        __syncwarp();
+#pragma unroll
+        for (int s = 1; s <= L / 2; ++s) {
+            const int src = seg_base + ((a + s) & (L - 1));
+            f2 dd, dx;  // (k0, p0), (k1, p1) and (k1, p0), (k0, p1)
 #pragma unroll
             for (int d = 0; d < DP; ++d) {
-                buf[d * 32 + lane] = x[d];
-                xs[d] = f2_pack(f2_hi(x[d]), f2_lo(x[d]));
+                const f2 q = buf[d * 32 + src];
+                const f2 e = f2_sub(x[d], q), es = f2_sub(xs[d], q);
+                dd = d == 0 ? f2_mul(e, e) : f2_fma(e, e, dd);
+                dx = d == 0 ? f2_mul(es, es) : f2_fma(es, es, dx);
             }
-            __syncwarp();
-#pragma unroll
-            for (int s = 1; s <= L / 2; ++s) {
-                const int src = seg_base + ((a + s) & (L - 1));
-                f2 dd, dx;  // (k0, p0), (k1, p1) and (k1, p0), (k0, p1)
-#pragma unroll
-                for (int d = 0; d < DP; ++d) {
-                    const f2 q = buf[d * 32 + src];
-                    const f2 e = f2_sub(x[d], q), es = f2_sub(xs[d], q);
-                    dd = d == 0 ? f2_mul(e, e) : f2_fma(e, e, dd);
-                    dx = d == 0 ? f2_mul(es, es) : f2_fma(es, es, dx);
-                }
-                m0 = fminf(m0, fminf(f2_lo(dd), f2_hi(dx)));
-                m1 = fminf(m1, fminf(f2_hi(dd), f2_lo(dx)));
-                if (2 * s != L) {
-                    const float p0 = fminf(f2_lo(dd), f2_lo(dx));
-                    const float p1 = fminf(f2_hi(dd), f2_hi(dx));
-                    const int back = seg_base + ((a - s) & (L - 1));
-                    m0 = fminf(m0, __shfl_sync(kFull, p0, back));
-                    m1 = fminf(m1, __shfl_sync(kFull, p1, back));
-                }
-            }
-        } else {
-#pragma unroll
-            for (int s = 1; s <= L / 2; ++s) {
-                const int src = seg_base + ((a + s) & (L - 1));
-                f2 dd, dx;  // (k0, p0), (k1, p1) and (k0, p1), (k1, p0)
-#pragma unroll
-                for (int d = 0; d < DP; ++d) {
-                    const float q0 = __shfl_sync(kFull, f2_lo(x[d]), src);
-                    const float q1 = __shfl_sync(kFull, f2_hi(x[d]), src);
-                    const f2 e = f2_sub(x[d], f2_pack(q0, q1)), es = f2_sub(x[d], f2_pack(q1, q0));
-                    dd = d == 0 ? f2_mul(e, e) : f2_fma(e, e, dd);
-                    dx = d == 0 ? f2_mul(es, es) : f2_fma(es, es, dx);
-                }
-                m0 = fminf(m0, fminf(f2_lo(dd), f2_lo(dx)));
-                m1 = fminf(m1, fminf(f2_hi(dd), f2_hi(dx)));
-                if (2 * s != L) {
-                    // the partner lane's minima over this lane's two robots
-                    const float p0 = fminf(f2_lo(dd), f2_hi(dx));
-                    const float p1 = fminf(f2_hi(dd), f2_lo(dx));
-                    const int back = seg_base + ((a - s) & (L - 1));
-                    m0 = fminf(m0, __shfl_sync(kFull, p0, back));
-                    m1 = fminf(m1, __shfl_sync(kFull, p1, back));
-                }
+            m0 = fminf(m0, fminf(f2_lo(dd), f2_hi(dx)));
+            m1 = fminf(m1, fminf(f2_hi(dd), f2_lo(dx)));
+            if (2 * s != L) {
+                // the partner lane's minima over this lane's two robots
+                const float p0 = fminf(f2_lo(dd), f2_lo(dx));
+                const float p1 = fminf(f2_hi(dd), f2_hi(dx));
+                const int back = seg_base + ((a - s) & (L - 1));
+                m0 = fminf(m0, __shfl_sync(kFull, p0, back));
+                m1 = fminf(m1, __shfl_sync(kFull, p1, back));
             }
         }
         float h = (real0 && m0 <= P.thr2 ? 1.0f : 0.0f) + (real1 && m1 <= P.thr2 ? 1.0f : 0.0f);

@@ -109,8 +109,8 @@ __device__ __noinline__ void batched_instance(const DevProblem& P, const BatchIn
                 const int j = base + warp * SPW + lane / LPS;
                 float f;
                 if constexpr (PAIRED)
-                    f = sample_fitness_paired<DYN, LPS, OBS, true>(P, S, sM, c3, j,
-                                                                   batched_xbuf(sList, C) + warp * kXbufPerWarp);
+                    f = sample_fitness_paired<DYN, LPS, OBS>(P, S, sM, c3, j,
+                                                             batched_xbuf(sList, C) + warp * kXbufPerWarp);
                 else f = sample_fitness_segment<DYN, SEG, OBS>(P, S, sM, c3, j);
                 if ((lane & (LPS - 1)) == 0 && j < N) sFit[j] = f;
             }

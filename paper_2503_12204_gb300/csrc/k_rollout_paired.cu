@@ -4,7 +4,8 @@
 // register-kernel warps are plentiful enough that half as many still keep
 // every scheduler busy.  A warp holds 32/L samples (L = SEG/2 lanes each);
 // the mean controls M = u_base + c dU are staged once per CTA in shared
-// memory; nothing but one float per sample leaves the SM.
+// memory, followed by each warp's position-exchange buffer; nothing but one
+// float per sample leaves the SM.
 #include <cmath>
 
 #include "d4orm_internal.h"
@@ -13,15 +14,11 @@
 namespace d4orm {
 
 constexpr int kK2bThreads = 256;
-// partners' positions through a per-warp shared-memory buffer (true) or
-// shuffles (false); the buffer measured 0.9 % faster on the 16-robot 3D
-// workload (86.5 against 87.2 us per launch inside the solve's graph)
-constexpr bool kK2bSmemExchange = true;
-
+// per-warp position buffers of sample_fitness_paired, after the mean controls
 template <int DYN>
 __host__ __device__ constexpr size_t k2b_xbuf_bytes_per_warp()
 {
-    return kK2bSmemExchange ? 2 * DynDims<DYN>::DP * 32 * sizeof(f2) : 0;
+    return 2 * DynDims<DYN>::DP * 32 * sizeof(f2);
 }
 
 template <int DYN, int L, bool OBS>
@@ -42,8 +39,7 @@ k_rollout_fitness_paired(const DevProblem P, const DevStep S, const float* __res
     // per-warp position buffers after the mean controls (8-byte aligned)
     f2* xbuf = reinterpret_cast<f2*>(sM + ((P.T * P.n * DU + 1) & ~1)) +
                (threadIdx.x >> 5) * (k2b_xbuf_bytes_per_warp<DYN>() / sizeof(f2));
-    const float f =
-        sample_fitness_paired<DYN, L, OBS, kK2bSmemExchange>(P, S, sM, iter_word(S, it_dev), j, xbuf);
+    const float f = sample_fitness_paired<DYN, L, OBS>(P, S, sM, iter_word(S, it_dev), j, xbuf);
     if ((lane & (L - 1)) == 0 && j < S.N) fitness[j] = f;
 }
 
